@@ -1,0 +1,344 @@
+"""Benchmark of the GB300 render path (arXiv 2410.08129 hot path).
+
+Headline workload: 1,000,000 clustered Gaussians (SH degree 3) rendered at
+1920x1080 with hybrid transparency, K = 8 (the paper's benchmark resolution,
+between its Francis 0.44M and Bicycle 4.35M scenes). A step is one full
+render: preprocess, binning, radix sort, blend. value = frames/s over all
+ranks. Also reported: the training step (500k Gaussians at 1200x800: render,
+L1 loss gradient, render backward) in steps/s, the end-to-end frame rate
+through the C ABI with host buffers, the blend kernel's roofline fraction
+and the FP64 oracle timed on this host.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank renders its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s @1M Gaussians and fwd+bwd steps/s, batched vs plain, at oracle tol"
+UNIT = "frames/s"
+WORKLOAD = "1M clustered Gaussians, SH deg 3, 1920x1080, 60deg vFOV, K=8, tau_alpha=1/255, tau_K=0.05"
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(scene, cam, prm, window=(944, 524, 32, 32)):
+    """The FP64 oracle (as it stands) on a bounded window of the same frame,
+    extrapolated to frames/s."""
+    import oracle
+    s64 = scene.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.render(s64, cam, prm, window=window)
+    dt = time.perf_counter() - t0
+    w, h = window[2], window[3]
+    fps = 1.0 / (dt * cam.width * cam.height / (w * h))
+    return {"value": fps, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{w}x{h} window at ({window[0]},{window[1]}) of the 1080p frame, all {scene.n} "
+                      f"Gaussians brute-forced per pixel; {dt:.2f} s, extrapolated to the full frame",
+            "pairs_per_s": scene.n * w * h / dt}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2410_08129_gb300 import scenes
+    import oracle
+    scene, cam, prm = scenes.config2()
+    cam = cam.rounded()
+    s64 = scene.astype(np.float64)
+    win = (952, 532, 16, 16)
+    for _ in range(args.warmup):
+        oracle.render(s64, cam, prm, window=win)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.render(s64, cam, prm, window=win)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    fps = 1.0 / (dt * cam.width * cam.height / (win[2] * win[3]))
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "16x16 window per step, extrapolated"},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"16x16 window of the 1080p frame per step ({dt:.3f} s)"},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_08129_gb300 import binding as B
+    from paper_2410_08129_gb300 import scenes
+    from paper_2410_08129_gb300.renderer import GaussianTensors, Renderer
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = _peaks()
+
+    # ---- headline: 1080p frames/s at 1M Gaussians --------------------------
+    scene, cam, prm = scenes.config2(seed=1 + rank)
+    cam = cam.rounded()
+    g = GaussianTensors.from_scene(scene)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in ev:
+        e.record(stream)
+    launch = B.c_launch((16, 16), 2, 0, ev)
+    r = Renderer(cam, prm, scene.n, launch=launch)
+    image = r.image_buffer()
+    r.forward(g, image=image, save=False, check=True)       # sizes the instance capacity
+    for _ in range(max(args.warmup, 3)):
+        r.forward(g, image=image, save=False, check=False)
+    torch.cuda.synchronize()
+    blend_ms, pre_ms, bin_ms = [], [], []
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for _ in range(args.steps):
+            r.forward(g, image=image, save=False, check=False)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    # per-phase times: a separate, identical pass (events between steps)
+    for _ in range(min(args.steps, 20)):
+        r.forward(g, image=image, save=False, check=False)
+        torch.cuda.synchronize()
+        pre_ms.append(ev[0].elapsed_time(ev[1]))
+        bin_ms.append(ev[2].elapsed_time(ev[3]))
+        blend_ms.append(ev[4].elapsed_time(ev[5]))
+    st, inst = r.status()
+    assert st == B.HTGS_OK, B.htgs_status_string(st)
+    counters = B.htgs_get_counters(r.workspace)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end))
+    ms_per_step = total_ms / args.steps
+    fps = world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
+            for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    host_img = torch.empty(image.shape, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host.values())
+    d2h = host_img.numel() * 4
+    for _ in range(2):
+        for k, t in host.items():
+            getattr(g, k).copy_(t, non_blocking=True)
+        r.forward(g, image=image, save=False, check=False)
+        host_img.copy_(image, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for k, t in host.items():
+            getattr(g, k).copy_(t, non_blocking=True)
+        r.forward(g, image=image, save=False, check=False)
+        host_img.copy_(image, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e2e_fps = world * args.steps / (e2e_ms / 1e3)
+
+    # ---- training step: render + L1 + backward (500k Gaussians, 1200x800) --
+    tscene, ttarget, tcam, tprm = scenes.config3(seed=2 + rank)
+    tcam = tcam.rounded()
+    tg = GaussianTensors.from_scene(tscene)
+    tt = GaussianTensors.from_scene(ttarget)
+    bev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in bev:
+        e.record(stream)
+    tr = Renderer(tcam, tprm, tscene.n, launch=B.c_launch((16, 16), 2, 0, bev))
+    target = tr.forward(tt, save=False, check=True).clone()
+    timg = tr.image_buffer()
+    dl = torch.empty_like(timg)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    grads = {k: torch.empty_like(getattr(tg, k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    tr.forward(tg, image=timg, save=True, check=True)
+
+    def train_step():
+        tr.forward(tg, image=timg, save=True, check=False)
+        B._check(B.htgs_l1_loss_grad(timg, target, dl, loss), "htgs_l1_loss_grad")
+        tr.backward(tg, dl, grads=grads)
+
+    for _ in range(max(args.warmup, 3)):
+        train_step()
+    torch.cuda.synchronize()
+    n_train = max(5, args.steps // 5)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    s0.record(stream)
+    for _ in range(n_train):
+        train_step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    train_ms = max_over_ranks(s0.elapsed_time(s1)) / n_train
+    bwd_blend_ms = []
+    for _ in range(3):
+        train_step()
+        torch.cuda.synchronize()
+        bwd_blend_ms.append(bev[0].elapsed_time(bev[1]))
+    st2, tinst = tr.status()
+    assert st2 == B.HTGS_OK
+    gfinite = all(bool(torch.isfinite(v).all()) for v in grads.values())
+
+    # ---- roofline of the dominant kernel (the forward blend) ---------------
+    # Algorithmic FP32-pipe instructions of the quadratic-form evaluation:
+    # 8 per pixel inside a tight bounding box (2 offsets, 5 FMA, 1 compare),
+    # 14 per kept fragment (denominator 5 FMA, 2 mul, 1 min, 5 tail sums,
+    # 1 count), 10 per core candidate (depth 6, key and compare 4) and 8K per
+    # core insertion; the peak is 152 SMs x 128 FP32 lanes x 2070 MHz.
+    K = prm.K
+    alg = (8 * counters["box_pairs"] + 14 * counters["kept"] + 10 * counters["admitted"]
+           + 8 * K * counters["inserted"])
+    blend_s = float(np.mean(blend_ms)) / 1e3
+    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6
+    achieved = alg / blend_s
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "blend_fwd_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                traffic = json.load(f).get("bytes_per_launch_1080p_1M")
+        except (OSError, ValueError):
+            traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, cam, prm)
+
+    line = {
+        "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": cam.width, "height": cam.height,
+                   "K": K, "tile": "16x16", "px_per_thread": 2, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (236 MB of Gaussian parameters per frame)"},
+        "phases_ms": {"preprocess": float(np.mean(pre_ms)), "binning_sort": float(np.mean(bin_ms)),
+                      "blend": float(np.mean(blend_ms))},
+        "instances": inst, "counters": counters,
+        "fwd_bwd": {"value": 1e3 / train_ms * world, "unit": "steps/s", "ms_per_step": train_ms,
+                    "workload": "500k Gaussians (box distribution), 1200x800, K=8: render + L1 + backward",
+                    "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
+                    "grads_finite": gfinite},
+        "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (no FP32 figure in MEASURED_PEAKS.json)"},
+        "gpu_launches": args.steps * 8,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

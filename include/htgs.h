@@ -1,0 +1,195 @@
+/*
+ * htgs.h -- C ABI of the GB300 (sm_103a) renderer for perspective-correct 3D
+ * Gaussian splatting with hybrid transparency (arXiv 2410.08129).
+ *
+ * Problem statement (Sec. 3.1-3.3): given Gaussians (mean, log-scales,
+ * quaternion, opacity logit, SH colour), a pinhole camera and the core size
+ * K, produce the image C of Eq. (15): each pixel blends the K nearest
+ * fragments exactly in depth order and the remaining tail
+ * order-independently behind them; render_backward returns dL/dparameters
+ * for a given dL/dimage.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller, unless the
+ *    entry point says otherwise. The library never allocates device memory
+ *    on the render path and never synchronises the stream it is given.
+ *  - Arrays are dense, row-major, float32, with the shapes stated below.
+ *  - Scratch memory is a caller-allocated workspace whose size comes from
+ *    htgs_workspace_size; the workspace must start on a 256-byte boundary.
+ *  - Every call returns an htgs_status; nothing throws across the ABI.
+ *    Errors found on the device (instance-capacity overflow, a bounded wait
+ *    that gave up) are recorded in the workspace and read back with
+ *    htgs_get_error after the stream has run.
+ *  - Calls sharing one workspace must not overlap on the GPU.
+ */
+#ifndef HTGS_H
+#define HTGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t htgs_status;
+#define HTGS_OK 0
+#define HTGS_ERR_INVALID_ARG 1   /* a pointer, size or parameter is out of range */
+#define HTGS_ERR_WORKSPACE 2     /* the workspace or saved buffer is too small */
+#define HTGS_ERR_OVERFLOW 3      /* more tile instances than instance_capacity; see htgs_get_error */
+#define HTGS_ERR_CUDA 4          /* a CUDA launch or runtime call failed */
+#define HTGS_ERR_TIMEOUT 5       /* a bounded device-side wait gave up */
+#define HTGS_ERR_NOT_SUPPORTED 6 /* e.g. K above the largest compiled core size */
+
+/* Largest core size K compiled into the blend kernels. */
+#define HTGS_MAX_K 32
+
+/* Scene parameters (Sec. 3.1). N Gaussians; n_coeff = (sh_degree + 1)^2.
+ *   means          N x 3        world-space mean mu
+ *   log_scales     N x 3        log s_u, log s_v, log s_w
+ *   quats          N x 4        (w, x, y, z), normalised inside the library
+ *   opacity_logits N            o = sigmoid(logit)
+ *   sh             N x n_coeff x 3, real SH in 3DGS order, degree <= 3
+ * Device pointers; float32; 16-byte aligned base addresses. */
+typedef struct {
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logits;
+    const float *sh;
+    int64_t n;
+    int32_t sh_degree;
+} htgs_gaussians;
+
+/* Gradient outputs, same shapes as htgs_gaussians. Device pointers. */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+} htgs_gaussians_grad;
+
+/* Pinhole camera, OpenCV axes (+x right, +y down, +z forward); world_to_cam
+ * is the row-major 4x4 model-view matrix M of Eq. (3) (last row 0 0 0 1).
+ * Pixel (i, j) has its centre at (i + 0.5, j + 0.5). Host memory (by value). */
+typedef struct {
+    float world_to_cam[16];
+    float fx, fy, cx, cy;
+    float z_near; /* a Gaussian whose cutoff ellipsoid reaches z <= z_near is culled */
+    int32_t width, height;
+} htgs_camera;
+
+/* Method parameters (Sec. 3.2 tau_alpha; Sec. 4.2 K and tau_K). */
+typedef struct {
+    int32_t K;        /* core size, 0 <= K <= HTGS_MAX_K (K = 0 is fully order-independent) */
+    float tau_alpha;  /* minimum fragment alpha; rho_c = 2 ln(o / tau_alpha) */
+    float tau_K;      /* minimum alpha for a fragment to enter the core */
+    float alpha_max;  /* alpha = min(o e^{-rho^2/2}, alpha_max), alpha_max < 1 */
+    float bg[3];      /* background colour c_bg */
+} htgs_params;
+
+/* Tuning knobs (none changes the result beyond float rounding order) and
+ * optional timing hooks. A NULL htgs_launch* or a zero field selects the
+ * default.
+ *   events  host array of 6 cudaEvent_t handles (created by the caller; any
+ *           entry may be NULL). htgs_render records [0]/[1] around the
+ *           preprocess, [2]/[3] around binning and sorting and [4]/[5]
+ *           around the blend; htgs_render_backward records [0]/[1] around
+ *           the blend adjoint and [2]/[3] around the preprocess adjoint. */
+typedef struct {
+    int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 16x8 or 8x8 */
+    int32_t px_per_thread;    /* pixels per thread in the blend: 1, 2 (default) or 4 */
+    int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */
+    void *events[6];
+} htgs_launch;
+
+/* Sizes of the caller-owned buffers for one camera.
+ *   instance_capacity  maximum number of (Gaussian, tile) instances
+ *   fwd_bytes    [out] workspace bytes needed by htgs_render / htgs_render_backward
+ *   saved_bytes  [out] per-pixel state htgs_render saves for the backward:
+ *                (7 + K) * width * height * 4 bytes
+ * Returns HTGS_ERR_INVALID_ARG for a bad size or parameter. */
+htgs_status htgs_workspace_size(int64_t n_gaussians, const htgs_camera *cam,
+                                const htgs_params *params, const htgs_launch *launch,
+                                int64_t instance_capacity, size_t *fwd_bytes, size_t *saved_bytes);
+
+/* Byte offsets of the internal buffers inside a workspace, for inspection by
+ * tests and tools; their contents are valid after htgs_render has run.
+ *   rec          n x 6 float4: per-Gaussian blend record
+ *   rect         n x uint2: covered tiles (tx0 | tx1 << 16, ty0 | ty1 << 16)
+ *   count        n x uint32: covered tile count
+ *   sorted_keys  capacity x uint32: tile keys after the radix sort
+ *   sorted_vals  capacity x uint32: the matching Gaussian ids
+ *   ranges       n_tiles x uint2: [start, end) of each tile in the sorted list
+ *   acc          n x 16 float: gradient accumulators of the blend adjoint
+ * Same argument rules as htgs_workspace_size; out is a host pointer. */
+typedef struct {
+    uint64_t rec, rect, count, sorted_keys, sorted_vals, ranges, acc;
+    int32_t n_tiles, tiles_x, tiles_y, tile_bits;
+} htgs_layout;
+
+htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam,
+                                  const htgs_params *params, const htgs_launch *launch,
+                                  int64_t instance_capacity, htgs_layout *out);
+
+/* Forward render, Sec. 3.2-3.3 and Eq. (15): preprocess (activations,
+ * T' = V P M T, tight bounding box, SH colour), tile binning and radix
+ * sort by tile key, and the per-pixel blend with a K-core and an
+ * order-independent tail.
+ *   image   [out] height x width x 3 float32, device
+ *   saved   [out] nullable; (7 + K) * width * height floats of per-pixel state
+ *           for htgs_render_backward (see htgs_workspace_size)
+ * The call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ * stream). If the instances exceed instance_capacity the blend is skipped
+ * and htgs_get_error reports HTGS_ERR_OVERFLOW with the required capacity. */
+htgs_status htgs_render(const htgs_gaussians *gaussians, const htgs_camera *cam,
+                        const htgs_params *params, const htgs_launch *launch,
+                        void *workspace, size_t workspace_bytes, int64_t instance_capacity,
+                        float *saved, float *image, void *stream);
+
+/* Backward of htgs_render, Sec. 3.3: re-traverses the tile lists of the
+ * preceding htgs_render (same workspace, same inputs), using the saved
+ * per-pixel core ids and tail accumulators; the tail's partial derivatives
+ * are per-pixel constants. Writes dL/d(every parameter) into `grads`
+ * (overwritten, not accumulated). dl_dimage: height x width x 3, device.
+ * No gradient flows through depth order, tau_alpha, tau_K or the culls. */
+htgs_status htgs_render_backward(const htgs_gaussians *gaussians, const htgs_camera *cam,
+                                 const htgs_params *params, const htgs_launch *launch,
+                                 void *workspace, size_t workspace_bytes, int64_t instance_capacity,
+                                 const float *saved, const float *dl_dimage,
+                                 const htgs_gaussians_grad *grads, void *stream);
+
+/* Reads the device status word of a workspace after synchronising `stream`.
+ *   status              [out] HTGS_OK, HTGS_ERR_OVERFLOW or HTGS_ERR_TIMEOUT
+ *   instances           [out] nullable; tile instances of the last render
+ * Host pointers. Clears nothing: the next htgs_render resets the word. */
+htgs_status htgs_get_error(void *workspace, size_t workspace_bytes, void *stream,
+                           htgs_status *status, int64_t *instances);
+
+/* Work counters of the last htgs_render on a workspace, after synchronising
+ * `stream`. counters (host, 4 x uint64):
+ *   [0] pixels inside the Gaussians' tight bounding boxes (sum over Gaussians)
+ *   [1] kept fragments, rho^2 <= rho_c, over all pixels
+ *   [2] kept fragments with alpha >= tau_K (core candidates)
+ *   [3] core insertions */
+htgs_status htgs_get_counters(void *workspace, size_t workspace_bytes, void *stream,
+                              uint64_t *counters);
+
+/* L1 photometric loss of a rendered image against a target (the training
+ * step's loss): loss = mean |image - target| over n = H*W*3 values and
+ * dl_dimage = sign(image - target) / n with sign(0) = 0.
+ *   image, target  n floats, device
+ *   dl_dimage      [out] n floats, device
+ *   loss           [out] 1 float, device (overwritten)
+ * Asynchronous on `stream`. */
+htgs_status htgs_l1_loss_grad(const float *image, const float *target, int64_t n, float *dl_dimage,
+                              float *loss, void *stream);
+
+/* Static string for a status code. */
+const char *htgs_status_string(htgs_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HTGS_H */

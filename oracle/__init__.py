@@ -94,7 +94,7 @@ class _Diag(ctypes.Structure):
                 ("core_gid", ctypes.c_void_p), ("T_core", ctypes.c_void_p),
                 ("T_tail", ctypes.c_void_p), ("A_tail", ctypes.c_void_p),
                 ("c_tail", ctypes.c_void_p), ("ambiguous", ctypes.c_void_p),
-                ("frag_hash", ctypes.c_void_p)]
+                ("frag_hash", ctypes.c_void_p), ("near_decision", ctypes.c_void_p)]
 
 
 def _load():
@@ -226,10 +226,11 @@ def render(scene, cam, params, window=None, diagnostics: bool = False):
         d = dict(n_frag=np.zeros((h, w), np.int32), n_core=np.zeros((h, w), np.int32),
                  core_gid=np.zeros((h, w, K), np.int32), T_core=np.zeros((h, w)),
                  T_tail=np.zeros((h, w)), A_tail=np.zeros((h, w)), c_tail=np.zeros((h, w, 3)),
-                 ambiguous=np.zeros((h, w), np.int32), frag_hash=np.zeros((h, w), np.uint64))
+                 ambiguous=np.zeros((h, w), np.int32), frag_hash=np.zeros((h, w), np.uint64),
+                 near_decision=np.zeros((h, w), np.int32))
         diag = _Diag(*[d[k].ctypes.data for k in ("n_frag", "n_core", "core_gid", "T_core",
                                                    "T_tail", "A_tail", "c_tail", "ambiguous",
-                                                   "frag_hash")])
+                                                   "frag_hash", "near_decision")])
     rc = lib.og_render(ctypes.byref(keep.g), ctypes.byref(c), ctypes.byref(p), ctypes.byref(win),
                        img.ctypes.data, ctypes.byref(diag) if diag is not None else None)
     if rc:

@@ -95,19 +95,31 @@ typedef struct {
     double *T_tail;        /* w*h */
     double *A_tail;        /* w*h: sum of tail alphas */
     double *c_tail;        /* w*h*3 */
-    int32_t *ambiguous;    /* w*h: bit mask of near-decision conditions */
+    int32_t *ambiguous;    /* w*h: near-decisions whose flip moves the colour by > 2e-5 */
     uint64_t *frag_hash;   /* w*h: order-independent hash of the fragment gid set */
+    int32_t *near_decision;/* w*h: every near-decision, whatever its effect on the colour */
 } og_pixel_diag;
 
-/* Near-decision flags (bits of og_pixel_diag.ambiguous). */
+/* Near-decision flags. A discrete decision that single precision may take
+   the other way: the cutoff rho^2 <= rho_c, core admission alpha >= tau_K,
+   the alpha clamp, and the depth order at and inside the core. Bits of
+   og_pixel_diag.near_decision mark every such event; bits of
+   og_pixel_diag.ambiguous mark those whose flip changes the pixel colour by
+   more than OG_EFFECT_TOL (found by blending the pixel again with the
+   decision flipped). */
 enum {
-    OG_AMB_CUTOFF = 1,   /* |rho^2 - rho_c| <= 1e-4 max(1, rho_c) */
-    OG_AMB_TAUK = 2,     /* |alpha - tau_K| <= 1e-5 */
+    OG_AMB_CUTOFF = 1,   /* |rho^2 - rho_c| <= 2e-5 max(1, rho_c) */
+    OG_AMB_TAUK = 2,     /* |alpha - tau_K| <= 2e-6 */
     OG_AMB_AMAX = 4,     /* |o e^{-rho^2/2} - alpha_max| <= 1e-6 */
     OG_AMB_CORE_EDGE = 8,/* K-th and (K+1)-th candidate depths within 1e-5 |z| */
     OG_AMB_CORE_TIE = 16,/* two adjacent core depths within 1e-5 |z| */
     OG_AMB_DEN = 32      /* ray nearly parallel to a flat splat: den tiny relative to its scale */
 };
+#define OG_CUTOFF_REL 2e-5
+#define OG_TAUK_ABS 2e-6
+#define OG_AMAX_ABS 1e-6
+#define OG_DEPTH_REL 1e-5
+#define OG_EFFECT_TOL 2e-5
 
 /* ------------------------------------------------------------------------ */
 /* Threading                                                                */
@@ -450,6 +462,7 @@ typedef struct {
     double z, alpha, a_raw, rho2;
     double c[3];
     int64_t gid;
+    int32_t force; /* 0: core admission by alpha >= tau_K; +1 / -1: forced in / out */
 } og_frag;
 
 static int og_frag_cmp(const void *pa, const void *pb) {
@@ -477,30 +490,36 @@ static int og_push(og_fragvec *v, const og_frag *x) {
 }
 
 /* Fragment decision for one pair: kept iff the ray meets the splat and
-   rho^2 <= rho_c (equivalently o e^{-rho^2/2} >= tau_alpha). */
+   rho^2 <= rho_c (equivalently o e^{-rho^2/2} >= tau_alpha). Returns 1 when
+   kept; *border is set when rho^2 lies within OG_CUTOFF_REL of rho_c (then fr
+   is filled even for a rejected pair, so that the flip can be evaluated). */
 static int og_fragment(const og_splat *sp, int64_t gid, double xs, double ys, const og_params *prm,
-                       og_frag *fr, int32_t *amb) {
+                       og_frag *fr, int32_t *amb, int *border) {
     og_eval ev;
+    if (border) *border = 0;
     if (!og_evaluate(sp, xs, ys, &ev)) return 0;
     const double rc = sp->rho_c;
-    if (amb && fabs(ev.rho2 - rc) <= 1e-4 * (rc > 1 ? rc : 1)) *amb |= OG_AMB_CUTOFF;
-    if (!(ev.rho2 <= rc)) return 0;
+    const int near_cut = fabs(ev.rho2 - rc) <= OG_CUTOFF_REL * (rc > 1 ? rc : 1);
+    if (border) *border = near_cut;
+    const int kept = ev.rho2 <= rc;
+    if (!kept && !near_cut) return 0;
     fr->z = ev.z;
     fr->rho2 = ev.rho2;
     fr->a_raw = sp->o * exp(-0.5 * ev.rho2);
     fr->alpha = fr->a_raw < prm->alpha_max ? fr->a_raw : prm->alpha_max;
-    if (amb) {
-        if (fabs(fr->alpha - prm->tau_K) <= 1e-5) *amb |= OG_AMB_TAUK;
-        if (fabs(fr->a_raw - prm->alpha_max) <= 1e-6) *amb |= OG_AMB_AMAX;
+    fr->force = 0;
+    for (int ch = 0; ch < 3; ++ch) fr->c[ch] = sp->rgb[ch];
+    fr->gid = gid;
+    if (kept && amb) {
+        if (fabs(fr->alpha - prm->tau_K) <= OG_TAUK_ABS) *amb |= OG_AMB_TAUK;
+        if (fabs(fr->a_raw - prm->alpha_max) <= OG_AMAX_ABS) *amb |= OG_AMB_AMAX;
         /* A kept pair whose den is tiny compared with |a||b| is a ray almost
            parallel to a flat splat; FP32 evaluation cannot resolve it. */
         double na = 0, nb = 0;
         for (int k = 0; k < 3; ++k) { na += ev.a[k] * ev.a[k]; nb += ev.b[k] * ev.b[k]; }
         if (ev.den <= 1e-8 * na * nb) *amb |= OG_AMB_DEN;
     }
-    for (int ch = 0; ch < 3; ++ch) fr->c[ch] = sp->rgb[ch];
-    fr->gid = gid;
-    return 1;
+    return kept;
 }
 
 /* Result of blending one pixel; the core is sorted by (z, gid). */
@@ -531,7 +550,7 @@ static void og_blend(og_fragvec *F, const og_params *prm, og_pixel_result *res) 
        to the front (keeping the rest as the tail). */
     int64_t nc = 0;
     for (int64_t i = 0; i < F->n; ++i)
-        if (F->f[i].alpha >= prm->tau_K) {
+        if (F->f[i].force > 0 || (F->f[i].force == 0 && F->f[i].alpha >= prm->tau_K)) {
             og_frag t = F->f[nc]; F->f[nc] = F->f[i]; F->f[i] = t;
             ++nc;
         }
@@ -539,10 +558,10 @@ static void og_blend(og_fragvec *F, const og_params *prm, og_pixel_result *res) 
     int64_t n_core = nc < K ? nc : K;
     if (nc > K && K > 0) {
         double zk = F->f[K - 1].z, zk1 = F->f[K].z;
-        if (fabs(zk1 - zk) <= 1e-5 * fabs(zk)) res->amb |= OG_AMB_CORE_EDGE;
+        if (fabs(zk1 - zk) <= OG_DEPTH_REL * fabs(zk)) res->amb |= OG_AMB_CORE_EDGE;
     }
     for (int64_t i = 0; i + 1 < n_core; ++i)
-        if (fabs(F->f[i + 1].z - F->f[i].z) <= 1e-5 * fabs(F->f[i].z)) res->amb |= OG_AMB_CORE_TIE;
+        if (fabs(F->f[i + 1].z - F->f[i].z) <= OG_DEPTH_REL * fabs(F->f[i].z)) res->amb |= OG_AMB_CORE_TIE;
     res->n_core = n_core;
 
     /* Core: sorted alpha blending, T_1 = 1, T_{i+1} = T_i (1 - alpha_i). */
@@ -581,9 +600,75 @@ typedef struct {
     int err;
 } og_render_ctx;
 
+/* Blends a copy of src[0..n) (og_blend reorders its input). */
+static void og_blend_copy(const og_frag *src, int64_t n, og_fragvec *scratch, const og_params *prm,
+                          og_pixel_result *res) {
+    scratch->n = 0;
+    for (int64_t i = 0; i < n; ++i) og_push(scratch, &src[i]);
+    memset(res, 0, sizeof(*res));
+    og_blend(scratch, prm, res);
+}
+
+static int og_moves(const og_pixel_result *a, const og_pixel_result *b) {
+    for (int ch = 0; ch < 3; ++ch)
+        if (fabs(a->C[ch] - b->C[ch]) > OG_EFFECT_TOL) return 1;
+    return 0;
+}
+
+/* Re-blends with each near-decision flipped; returns the bits whose flip
+   moves the colour by more than OG_EFFECT_TOL. */
+static int32_t og_effects(const og_fragvec *F0, const og_fragvec *Bd, const og_fragvec *Fs,
+                          const og_pixel_result *res, const og_params *prm, og_fragvec *work,
+                          og_fragvec *scratch) {
+    int32_t amb = 0;
+    og_pixel_result alt;
+    /* Cutoff: drop a kept borderline fragment, or add a rejected one. */
+    for (int64_t b = 0; b < Bd->n && !(amb & OG_AMB_CUTOFF); ++b) {
+        const og_frag *x = &Bd->f[b];
+        work->n = 0;
+        int present = 0;
+        for (int64_t i = 0; i < F0->n; ++i) {
+            if (F0->f[i].gid == x->gid) { present = 1; continue; }
+            og_push(work, &F0->f[i]);
+        }
+        if (!present) og_push(work, x);
+        og_blend_copy(work->f, work->n, scratch, prm, &alt);
+        if (og_moves(&alt, res)) amb |= OG_AMB_CUTOFF;
+    }
+    /* Core admission: force the opposite side of tau_K. */
+    for (int64_t i = 0; i < F0->n && !(amb & OG_AMB_TAUK); ++i) {
+        if (fabs(F0->f[i].alpha - prm->tau_K) > OG_TAUK_ABS) continue;
+        work->n = 0;
+        for (int64_t k = 0; k < F0->n; ++k) og_push(work, &F0->f[k]);
+        work->f[i].force = F0->f[i].alpha >= prm->tau_K ? -1 : 1;
+        og_blend_copy(work->f, work->n, scratch, prm, &alt);
+        if (og_moves(&alt, res)) amb |= OG_AMB_TAUK;
+    }
+    /* Depth order: swap the depths of close neighbours among the sorted
+       candidates Fs (core and first excluded candidate). */
+    const int64_t K = prm->K;
+    for (int64_t i = 0; i + 1 < Fs->n && i < K; ++i) {
+        const og_frag *a = &Fs->f[i], *b = &Fs->f[i + 1];
+        if (fabs(b->z - a->z) > OG_DEPTH_REL * fabs(a->z)) continue;
+        const int32_t bit = (i + 1 == K) ? OG_AMB_CORE_EDGE : OG_AMB_CORE_TIE;
+        if (amb & bit) continue;
+        work->n = 0;
+        for (int64_t k = 0; k < F0->n; ++k) {
+            og_frag f = F0->f[k];
+            if (f.gid == a->gid) f.z = b->z;
+            else if (f.gid == b->gid) f.z = a->z;
+            og_push(work, &f);
+        }
+        og_blend_copy(work->f, work->n, scratch, prm, &alt);
+        /* Equal depths after the swap are ordered by gid; make the swap strict. */
+        if (og_moves(&alt, res)) amb |= bit;
+    }
+    return amb;
+}
+
 static void og_render_task(void *vctx, int64_t b, int64_t e) {
     og_render_ctx *c = (og_render_ctx *)vctx;
-    og_fragvec F = {0};
+    og_fragvec F = {0}, F0 = {0}, Bd = {0}, work = {0}, scratch = {0};
     const int K = c->prm->K;
     for (int64_t pix = b; pix < e; ++pix) {
         int64_t li = pix % c->win.w, lj = pix / c->win.w;
@@ -592,16 +677,31 @@ static void og_render_task(void *vctx, int64_t b, int64_t e) {
         og_pixel_result res;
         memset(&res, 0, sizeof(res));
         F.n = 0;
+        Bd.n = 0;
         for (int64_t g = 0; g < c->n; ++g) {
             if (!c->sp[g].valid) continue;
             og_frag fr;
-            if (og_fragment(&c->sp[g], g, xs, ys, c->prm, &fr, &res.amb))
-                if (og_push(&F, &fr)) { c->err = 1; free(F.f); return; }
+            int border = 0;
+            int kept = og_fragment(&c->sp[g], g, xs, ys, c->prm, &fr, &res.amb, &border);
+            if (kept && og_push(&F, &fr)) { c->err = 1; goto out; }
+            if (border && c->diag && og_push(&Bd, &fr)) { c->err = 1; goto out; }
         }
+        F0.n = 0;
+        if (c->diag)
+            for (int64_t i = 0; i < F.n; ++i) og_push(&F0, &F.f[i]);
         og_blend(&F, c->prm, &res);
         for (int ch = 0; ch < 3; ++ch) c->image[pix * 3 + ch] = res.C[ch];
         og_pixel_diag *d = c->diag;
         if (d) {
+            int32_t near = res.amb | (Bd.n ? OG_AMB_CUTOFF : 0);
+            /* Sorted candidates = the front of F after og_blend. */
+            og_fragvec Fs = {F.f, 0, 0};
+            int64_t nc = 0;
+            while (nc < F.n && (F.f[nc].force > 0 || (F.f[nc].force == 0 && F.f[nc].alpha >= c->prm->tau_K))) ++nc;
+            Fs.n = nc < K + 1 ? nc : K + 1;
+            int32_t amb = near & (OG_AMB_DEN);
+            if (near & (OG_AMB_CUTOFF | OG_AMB_TAUK | OG_AMB_CORE_EDGE | OG_AMB_CORE_TIE))
+                amb |= og_effects(&F0, &Bd, &Fs, &res, c->prm, &work, &scratch);
             if (d->n_frag) d->n_frag[pix] = (int32_t)res.n_frag;
             if (d->n_core) d->n_core[pix] = (int32_t)res.n_core;
             if (d->core_gid)
@@ -612,11 +712,17 @@ static void og_render_task(void *vctx, int64_t b, int64_t e) {
             if (d->A_tail) d->A_tail[pix] = res.A_tail;
             if (d->c_tail)
                 for (int ch = 0; ch < 3; ++ch) d->c_tail[pix * 3 + ch] = res.c_tail[ch];
-            if (d->ambiguous) d->ambiguous[pix] = res.amb;
+            if (d->ambiguous) d->ambiguous[pix] = amb;
+            if (d->near_decision) d->near_decision[pix] = near;
             if (d->frag_hash) d->frag_hash[pix] = res.hash;
         }
     }
+out:
     free(F.f);
+    free(F0.f);
+    free(Bd.f);
+    free(work.f);
+    free(scratch.f);
 }
 
 static int og_check(const og_camera *cam, const og_params *prm, const og_window *win) {
@@ -701,7 +807,7 @@ static void og_bwd_pixel_task(void *vctx, int64_t b, int64_t e) {
         for (int64_t g = 0; g < c->n; ++g) {
             if (!c->sp[g].valid) continue;
             og_frag fr;
-            if (og_fragment(&c->sp[g], g, xs, ys, c->prm, &fr, NULL))
+            if (og_fragment(&c->sp[g], g, xs, ys, c->prm, &fr, NULL, NULL))
                 if (og_push(&F, &fr)) { c->err = 1; free(F.f); return; }
         }
         og_blend(&F, c->prm, &res);

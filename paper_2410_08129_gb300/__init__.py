@@ -2,10 +2,18 @@
 transparency (arXiv 2410.08129).
 
 The rendering path runs entirely in hand-written sm_103a CUDA kernels behind a
-C-ABI library (``include/htgs.h``); this package is the thin Python binding
-over it. Importing the package does not load the CUDA library; the first call
-into the binding does, and it raises if the library is missing.
+C-ABI library (``include/htgs.h``); ``binding`` is the thin ctypes layer over
+it and ``renderer`` adds workspace management and a torch.autograd.Function.
+Importing the package does not load the CUDA library; the first call into the
+binding does, and it raises if the library is missing.
 """
 from . import scenes  # noqa: F401  (seeded input generators; no method arithmetic)
 
-__all__ = ["scenes"]
+__all__ = ["scenes", "binding", "renderer", "build"]
+
+
+def __getattr__(name):
+    if name in ("binding", "renderer", "build"):
+        import importlib
+        return importlib.import_module(f".{name}", __name__)
+    raise AttributeError(name)

@@ -1,0 +1,228 @@
+"""Thin ctypes binding over the C ABI of include/htgs.h.
+
+The functions named like the C entry points (htgs_render, ...) only marshal
+arguments: torch tensors become device pointers, scenes.Camera / Params
+become the C structs, and torch's current CUDA stream is passed through.
+Every step of the render path runs in the CUDA library; if the library is
+missing the first call raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+HTGS_OK = 0
+HTGS_ERR_INVALID_ARG = 1
+HTGS_ERR_WORKSPACE = 2
+HTGS_ERR_OVERFLOW = 3
+HTGS_ERR_CUDA = 4
+HTGS_ERR_TIMEOUT = 5
+HTGS_ERR_NOT_SUPPORTED = 6
+HTGS_MAX_K = 32
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32)]
+
+
+class GaussiansGrad(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("world_to_cam", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("z_near", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("tau_alpha", ctypes.c_float), ("tau_K", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("px_per_thread", ctypes.c_int32), ("depth_bits", ctypes.c_int32),
+                ("events", ctypes.c_void_p * 6)]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("rec", ctypes.c_uint64), ("rect", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("sorted_keys", ctypes.c_uint64), ("sorted_vals", ctypes.c_uint64),
+                ("ranges", ctypes.c_uint64), ("acc", ctypes.c_uint64), ("n_tiles", ctypes.c_int32),
+                ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("tile_bits", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libhtgs.so (building it first if it is absent). Raises when the
+    library cannot be built or loaded: there is no other implementation."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            L.htgs_workspace_size.argtypes = [ctypes.c_int64, P(Camera), P(Params), P(Launch),
+                                              ctypes.c_int64, P(ctypes.c_size_t), P(ctypes.c_size_t)]
+            L.htgs_render.argtypes = [P(Gaussians), P(Camera), P(Params), P(Launch), ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+            L.htgs_render_backward.argtypes = [P(Gaussians), P(Camera), P(Params), P(Launch),
+                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64,
+                                               ctypes.c_void_p, ctypes.c_void_p, P(GaussiansGrad),
+                                               ctypes.c_void_p]
+            L.htgs_get_error.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                         P(ctypes.c_int32), P(ctypes.c_int64)]
+            L.htgs_get_counters.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                             ctypes.c_void_p]
+            L.htgs_workspace_layout.argtypes = [ctypes.c_int64, P(Camera), P(Params), P(Launch),
+                                                ctypes.c_int64, P(Layout)]
+            L.htgs_l1_loss_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.htgs_l1_loss_grad.restype = ctypes.c_int32
+            L.htgs_status_string.argtypes = [ctypes.c_int32]
+            L.htgs_status_string.restype = ctypes.c_char_p
+            for f in ("htgs_workspace_size", "htgs_render", "htgs_render_backward", "htgs_get_error",
+                      "htgs_workspace_layout", "htgs_get_counters"):
+                getattr(L, f).restype = ctypes.c_int32
+            _lib = L
+    return _lib
+
+
+class HTGSError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {htgs_status_string(status)} ({status})")
+        self.status = status
+
+
+def _check(status: int, what: str):
+    if status != HTGS_OK:
+        raise HTGSError(status, what)
+
+
+def c_camera(cam) -> Camera:
+    c = Camera()
+    M = np.asarray(cam.world_to_cam, np.float64).reshape(16)
+    for i in range(16):
+        c.world_to_cam[i] = float(M[i])
+    c.fx, c.fy, c.cx, c.cy, c.z_near = (float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                                        float(cam.z_near))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def c_params(p) -> Params:
+    q = Params()
+    q.K = int(p.K)
+    q.tau_alpha, q.tau_K, q.alpha_max = float(p.tau_alpha), float(p.tau_K), float(p.alpha_max)
+    for i in range(3):
+        q.bg[i] = float(p.bg[i])
+    return q
+
+
+def c_launch(tile=(16, 16), px_per_thread=0, depth_bits=0, events=None) -> Launch:
+    """events: up to 6 torch.cuda.Event(enable_timing=True) (or None) recorded
+    around the render phases, see htgs_launch in include/htgs.h."""
+    L = Launch(int(tile[0]), int(tile[1]), int(px_per_thread), int(depth_bits))
+    for i, e in enumerate(events or []):
+        L.events[i] = e.cuda_event if e is not None else None
+    return L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def c_gaussians(means, log_scales, quats, logits, sh, sh_degree) -> Gaussians:
+    for t in (means, log_scales, quats, logits, sh):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("Gaussian parameters must be contiguous float32 CUDA tensors")
+    return Gaussians(_ptr(means).value, _ptr(log_scales).value, _ptr(quats).value, _ptr(logits).value,
+                     _ptr(sh).value, int(means.shape[0]), int(sh_degree))
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# -- entry points with the C names -------------------------------------------
+
+def htgs_status_string(status: int) -> str:
+    return lib().htgs_status_string(int(status)).decode()
+
+
+def htgs_workspace_size(n, cam, params, launch, capacity):
+    fwd = ctypes.c_size_t()
+    saved = ctypes.c_size_t()
+    st = lib().htgs_workspace_size(int(n), ctypes.byref(c_camera(cam)), ctypes.byref(c_params(params)),
+                                   ctypes.byref(launch) if launch is not None else None, int(capacity),
+                                   ctypes.byref(fwd), ctypes.byref(saved))
+    _check(st, "htgs_workspace_size")
+    return int(fwd.value), int(saved.value)
+
+
+def htgs_workspace_layout(n, cam, params, launch, capacity) -> Layout:
+    out = Layout()
+    st = lib().htgs_workspace_layout(int(n), ctypes.byref(c_camera(cam)), ctypes.byref(c_params(params)),
+                                     ctypes.byref(launch) if launch is not None else None, int(capacity),
+                                     ctypes.byref(out))
+    _check(st, "htgs_workspace_layout")
+    return out
+
+
+def htgs_render(gaussians: Gaussians, cam, params, launch, workspace, capacity, saved, image, stream=None):
+    st = lib().htgs_render(ctypes.byref(gaussians), ctypes.byref(c_camera(cam)), ctypes.byref(c_params(params)),
+                           ctypes.byref(launch) if launch is not None else None,
+                           _ptr(workspace), workspace.numel() * workspace.element_size(), int(capacity),
+                           _ptr(saved) if saved is not None else None, _ptr(image), _stream(stream))
+    return int(st)
+
+
+def htgs_render_backward(gaussians: Gaussians, cam, params, launch, workspace, capacity, saved, dl_dimage,
+                         grads: GaussiansGrad, stream=None):
+    st = lib().htgs_render_backward(ctypes.byref(gaussians), ctypes.byref(c_camera(cam)),
+                                    ctypes.byref(c_params(params)),
+                                    ctypes.byref(launch) if launch is not None else None, _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), int(capacity), _ptr(saved),
+                                    _ptr(dl_dimage), ctypes.byref(grads), _stream(stream))
+    return int(st)
+
+
+def htgs_get_error(workspace, stream=None):
+    status = ctypes.c_int32()
+    inst = ctypes.c_int64()
+    st = lib().htgs_get_error(_ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream(stream), ctypes.byref(status), ctypes.byref(inst))
+    _check(st, "htgs_get_error")
+    return int(status.value), int(inst.value)
+
+
+def htgs_get_counters(workspace, stream=None):
+    out = (ctypes.c_uint64 * 4)()
+    st = lib().htgs_get_counters(_ptr(workspace), workspace.numel() * workspace.element_size(),
+                                 _stream(stream), out)
+    _check(st, "htgs_get_counters")
+    return dict(box_pairs=int(out[0]), kept=int(out[1]), admitted=int(out[2]), inserted=int(out[3]))
+
+
+def htgs_l1_loss_grad(image, target, dl_dimage, loss, stream=None):
+    st = lib().htgs_l1_loss_grad(_ptr(image), _ptr(target), int(image.numel()), _ptr(dl_dimage), _ptr(loss),
+                                 _stream(stream))
+    return int(st)

@@ -1,0 +1,331 @@
+// binning.cu -- tile binning and sorting (arXiv 2410.08129, Sec. 4.3: one
+// instance per covered (Gaussian, tile) keyed by the tile id, with no global
+// depth sort).
+//
+//   scan_blocks  exclusive scan of the preprocess block sums; overflow check
+//   emit         one thread group per Gaussian writes (tile key, gid) for each
+//                covered tile, load-balanced across the lanes of a warp
+//   histogram    digit histograms of every radix pass in one read of the keys
+//   onesweep     one stable scatter per 8-bit digit; the block prefix comes
+//                from a decoupled look-back whose waits are bounded
+//   ranges       [start, end) of every tile in the sorted keys
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace htgs {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the per-block instance counts (one CTA).
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(BinArgs a) {
+    __shared__ uint64_t warp_tot[kScanThreads / 32];
+    const int nb = a.n_blocks;
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * per;
+    uint64_t local = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) local += a.block_sums[b0 + k];
+    // Block-wide exclusive scan of `local`.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t v = warp_tot[lane];
+        uint64_t vi = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= o) vi += t;
+        }
+        warp_tot[lane] = vi - v;
+    }
+    __syncthreads();
+    uint64_t run = warp_tot[warp] + incl - local;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) {
+            uint32_t c = a.block_sums[b0 + k];
+            a.block_sums[b0 + k] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+            run += c;
+        }
+    if (threadIdx.x == kScanThreads - 1) {
+        const uint64_t total = run;
+        a.status[kStInstLo] = (int)(uint32_t)(total & 0xffffffffull);
+        a.status[kStInstHi] = (int)(uint32_t)(total >> 32);
+        if (total > (uint64_t)a.capacity) {
+            set_error(a.status, HTGS_ERR_OVERFLOW);
+            a.total[0] = 0;
+        } else {
+            a.total[0] = (uint32_t)total;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Emit: instance j of Gaussian g covers tile (tx0 + r % w, ty0 + r / w).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPreThreads) emit_kernel(BinArgs a) {
+    __shared__ uint32_t warp_tot[kPreThreads / 32];
+    if (a.status[kStError] == HTGS_ERR_OVERFLOW) return;
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t c = i < a.n ? a.count[i] : 0u;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - c;
+    const uint32_t wtot = __shfl_sync(kFull, incl, 31);
+    if (lane == 0) warp_tot[warp] = wtot;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += warp_tot[w];
+    const uint64_t base = (uint64_t)a.block_sums[blockIdx.x] + woff;
+    const uint2 r = c ? a.rect[i] : make_uint2(0u, 0u);
+    const uint32_t gid0 = (uint32_t)((int64_t)blockIdx.x * kPreThreads + warp * 32);
+    const int iters = (int)((wtot + 31) / 32);
+    for (int it = 0; it < iters; ++it) {
+        const uint32_t j = (uint32_t)it * 32 + lane;
+        // Owner lane: the largest l with excl[l] <= j (lanes with no instances
+        // share their offset with the next lane that has some).
+        int L = 0;
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = L + step;
+            const uint32_t v = __shfl_sync(kFull, excl, cand);
+            if (v <= j) L = cand;
+        }
+        const uint32_t rx = __shfl_sync(kFull, r.x, L);
+        const uint32_t ry = __shfl_sync(kFull, r.y, L);
+        const uint32_t eL = __shfl_sync(kFull, excl, L);
+        if (j < wtot) {
+            const uint32_t rr = j - eL;
+            const uint32_t tx0 = rx & 0xffffu, tx1 = rx >> 16;
+            const uint32_t w = tx1 - tx0 + 1;
+            const uint32_t tx = tx0 + rr % w;
+            const uint32_t ty = (ry & 0xffffu) + rr / w;
+            const uint64_t pos = base + j;
+            if (pos < (uint64_t)a.capacity) {
+                a.keys[pos] = (ty * (uint32_t)a.tiles.tiles_x + tx) << a.tiles.depth_bits;
+                a.vals[pos] = gid0 + (uint32_t)L;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort: digit histograms for all passes in one read.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) histogram_kernel(SortArgs a) {
+    __shared__ uint32_t h[kMaxPasses * kRadix];
+    for (int k = threadIdx.x; k < a.passes * kRadix; k += kSortThreads) h[k] = 0;
+    __syncthreads();
+    const uint32_t total = *a.total;
+    const uint32_t *keys = a.keys[0];
+    for (uint32_t idx = blockIdx.x * kSortThreads + threadIdx.x; idx < total;
+         idx += gridDim.x * kSortThreads) {
+        const uint32_t k = keys[idx];
+        for (int p = 0; p < a.passes; ++p) atomicAdd(&h[p * kRadix + ((k >> (p * kRadixBits)) & (kRadix - 1))], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.passes * kRadix; k += kSortThreads)
+        if (h[k]) atomicAdd(&a.ghist[k], h[k]);
+}
+
+// ---------------------------------------------------------------------------
+// One stable scatter pass. Blocks take tickets in launch order so that every
+// block they wait on is already resident; waits are bounded.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int pass, int src) {
+    __shared__ uint32_t s_whist[kSortWarps][kRadix];
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_scan[kRadix];
+    __shared__ uint32_t s_wsum[kSortWarps];
+    __shared__ int s_ticket;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_ticket = (int)atomicAdd(&a.tickets[pass], 1u);
+    for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
+    __syncthreads();
+    const int t = s_ticket;
+    const uint32_t total = *a.total;
+    const uint32_t used = (total + kSortTile - 1) / kSortTile;
+    if ((uint32_t)t >= used) return;
+    const int shift = pass * kRadixBits;
+    const uint32_t *kin = a.keys[src], *vin = a.vals[src];
+    uint32_t *kout = a.keys[src ^ 1], *vout = a.vals[src ^ 1];
+
+    // Global digit offsets: exclusive scan of this pass's histogram.
+    {
+        const uint32_t v = a.ghist[pass * kRadix + tid];
+        uint32_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int w = 0; w < warp; ++w) off += s_wsum[w];
+        s_scan[tid] = off + incl - v;
+    }
+
+    // Stable per-warp ranking: item order is (warp, iteration, lane).
+    const uint32_t wbase = (uint32_t)t * kSortTile + (uint32_t)warp * 32 * kSortItems;
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t idx = wbase + it * 32 + lane;
+        const bool valid = idx < total;
+        key[it] = valid ? kin[idx] : 0u;
+        val[it] = valid ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t idx = wbase + it * 32 + lane;
+        const bool valid = idx < total;
+        const uint32_t vmask = __ballot_sync(kFull, valid);
+        uint32_t r = 0;
+        if (valid) {
+            const uint32_t d = (key[it] >> shift) & (kRadix - 1);
+            const uint32_t peers = __match_any_sync(vmask, d);
+            const uint32_t below = peers & lanemask_lt();
+            const uint32_t prev = s_whist[warp][d];
+            r = prev + __popc(below);
+            __syncwarp(vmask);
+            if (below == 0) s_whist[warp][d] = prev + __popc(peers);
+        }
+        __syncwarp();
+        rank[it] = r;
+    }
+    __syncthreads();
+
+    // Per digit: prefix over warps, block count, decoupled look-back.
+    {
+        const int d = tid;
+        uint32_t run = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = s_whist[w][d];
+            s_whist[w][d] = run;
+            run += c;
+        }
+        uint32_t *lb = a.lookback + ((size_t)pass * a.n_sort_blocks) * kRadix;
+        uint32_t excl = 0;
+        if (t == 0) {
+            st_relaxed(&lb[d], kFlagInc | run);
+        } else {
+            st_relaxed(&lb[(size_t)t * kRadix + d], kFlagAgg | run);
+            int pred = t - 1;
+            uint32_t spins = 0;
+            while (pred >= 0) {
+                const uint32_t v = ld_relaxed(&lb[(size_t)pred * kRadix + d]);
+                const uint32_t flag = v & ~kCountMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        set_error(a.status, HTGS_ERR_TIMEOUT);
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(64);
+                    continue;
+                }
+                excl += v & kCountMask;
+                if (flag == kFlagInc) break;
+                --pred;
+            }
+            st_relaxed(&lb[(size_t)t * kRadix + d], kFlagInc | ((excl + run) & kCountMask));
+        }
+        s_base[d] = s_scan[d] + excl;
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t idx = wbase + it * 32 + lane;
+        if (idx < total) {
+            const uint32_t d = (key[it] >> shift) & (kRadix - 1);
+            const uint32_t pos = s_base[d] + s_whist[warp][d] + rank[it];
+            if (pos < total) {  // always true unless a bounded wait gave up
+                kout[pos] = key[it];
+                vout[pos] = val[it];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile ranges from the sorted keys.
+// ---------------------------------------------------------------------------
+__global__ void ranges_kernel(RangeArgs a) {
+    const uint32_t total = *a.total;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t t = a.keys[i] >> a.shift;
+        if (t >= (uint32_t)a.n_tiles) continue;
+        if (i == 0 || (a.keys[i - 1] >> a.shift) != t) a.ranges[t].x = i;
+        if (i + 1 == total || (a.keys[i + 1] >> a.shift) != t) a.ranges[t].y = i + 1;
+    }
+}
+
+} // namespace
+
+void launch_scan_blocks(const BinArgs &a, cudaStream_t s) {
+    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(a);
+}
+
+void launch_emit(const BinArgs &a, cudaStream_t s) {
+    if (a.n_blocks > 0) emit_kernel<<<a.n_blocks, kPreThreads, 0, s>>>(a);
+}
+
+int launch_sort(const SortArgs &a, cudaStream_t s) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int hist_blocks = std::min<int64_t>((int64_t)sms * 4, (a.capacity + kSortThreads - 1) / kSortThreads + 1);
+    histogram_kernel<<<hist_blocks, kSortThreads, 0, s>>>(a);
+    int src = 0;
+    for (int p = 0; p < a.passes; ++p) {
+        onesweep_kernel<<<a.n_sort_blocks, kSortThreads, 0, s>>>(a, p, src);
+        src ^= 1;
+    }
+    return src;
+}
+
+void launch_ranges(RangeArgs a, int n_tiles, cudaStream_t s) {
+    a.n_tiles = n_tiles;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ranges_kernel<<<sms * 8, 256, 0, s>>>(a);
+    (void)n_tiles;
+}
+
+} // namespace htgs

@@ -1,0 +1,112 @@
+// common.cuh -- shared device helpers and the internal launch structures of
+// the sm_103a renderer (arXiv 2410.08129, Sec. 3.2-3.3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/htgs.h"
+
+namespace htgs {
+
+// ---------------------------------------------------------------------------
+// Internal argument blocks (passed by value as kernel parameters).
+// ---------------------------------------------------------------------------
+
+struct CamArgs {
+    float M[12];          // rows 0..2 of the row-major world-to-camera matrix
+    float fx, fy, cx, cy; // pinhole intrinsics in window coordinates
+    float z_near;
+    float centre[3];      // camera centre in world space
+    int width, height;
+};
+
+struct ParamArgs {
+    int K;
+    float tau_alpha, tau_K, alpha_max;
+    float bg[3];
+};
+
+struct TileArgs {
+    int tile_w, tile_h;
+    int tiles_x, tiles_y;
+    int n_tiles;
+    int tile_bits;   // bits of the sort key holding the tile id
+    int depth_bits;  // low key bits holding quantised depth
+};
+
+// Per-Gaussian blend record: 24 floats = 96 bytes = 6 float4.
+//   [0] xc, yc, q0, q1        screen centre of the bounding box; Q coefficients
+//   [1] q2, q3, q4, q5
+//   [2] d0, d1, d2, d3        D = ||d||^2 coefficients
+//   [3] d4, d5, z0, z1        Z = (view depth) * D coefficients
+//   [4] z2, z3, z4, z5
+//   [5] r, g, b, rho_c        colour and cutoff
+// Each quadratic is c0 + c1 x' + c2 y' + c3 x'^2 + c4 x'y' + c5 y'^2 in the
+// offsets (x', y') = (x - xc, y - yc) of the pixel centre. With
+// N = ||m||^2 (m the Pluecker moment), Q = log2(e) (rho_c D - N) / 2, so
+// that rho^2 = N / D <= rho_c <=> Q >= 0 and
+// alpha = o e^{-rho^2/2} = tau_alpha * 2^{Q / D}.
+constexpr int kRecF4 = 6;
+
+// Device status word layout (int32 array at the front of the workspace).
+enum StatusSlot {
+    kStError = 0,      // htgs_status of the last device-side failure (0 = none)
+    kStInstLo = 1,     // total instances of the last render (low 32 bits)
+    kStInstHi = 2,
+    kStSlots = 16
+};
+
+// ---------------------------------------------------------------------------
+// Small numeric helpers. The forward and backward must evaluate alpha and
+// depth bit-identically, so these use explicit round-to-nearest intrinsics
+// that the compiler cannot re-associate or contract differently.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// c0 + x (c1 + c3 x + c4 y) + y (c2 + c5 y), fixed evaluation order.
+__device__ __forceinline__ float quad_eval(float c0, float c1, float c2, float c3, float c4,
+                                           float c5, float x, float y) {
+    float tx = __fmaf_rn(c4, y, __fmaf_rn(c3, x, c1));
+    float ty = __fmaf_rn(c5, y, c2);
+    return __fmaf_rn(y, ty, __fmaf_rn(x, tx, c0));
+}
+
+__device__ __forceinline__ unsigned long long make_key(float z, uint32_t gid) {
+    // z > 0 for every kept fragment (the near cull keeps whole cutoff
+    // ellipsoids in front of the camera); non-negative floats order like
+    // their bit patterns. Ties break by gid.
+    return ((unsigned long long)__float_as_uint(fmaxf(z, 0.0f)) << 32) | gid;
+}
+
+__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+
+// Work counters (uint64 array in the workspace, zeroed by every render).
+enum StatSlot {
+    kStatBoxPairs = 0,   // sum over Gaussians of the pixels inside the tight bounding box
+    kStatKept = 1,       // fragments with rho^2 <= rho_c (every pixel)
+    kStatAdmitted = 2,   // kept fragments with alpha >= tau_K
+    kStatInserted = 3,   // core insertions
+    kStatSlots = 8
+};
+
+__device__ __forceinline__ void set_error(int *status, int code) {
+    atomicCAS(status + kStError, 0, code);
+}
+
+} // namespace htgs

@@ -1,0 +1,437 @@
+// preprocess.cu -- per-Gaussian setup and its adjoint (arXiv 2410.08129,
+// Sec. 3.1 scene representation, Sec. 3.2 Eq. (3) T' = V P M T, the tight
+// screen bounding box and the opacity-aware cutoff).
+//
+// One thread per Gaussian. The forward writes the 96-byte blend record (see
+// common.cuh), the covered tile rectangle and the tile count; the backward
+// turns the per-Gaussian gradient accumulators of the blend adjoint into
+// gradients of the means, log-scales, quaternions, opacity logits and SH.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace htgs {
+
+namespace {
+
+// Real spherical harmonics up to degree 3 in 3DGS order (m = -l..l), as
+// polynomials of the unit direction. Constants are the closed forms
+// Y00 = 1/(2 sqrt(pi)), Y1 = sqrt(3/(4 pi)), Y2 = sqrt(15/(4 pi)),
+// sqrt(5/(16 pi)), sqrt(15/(16 pi)), Y3 = sqrt(35/(32 pi)), sqrt(105/(4 pi)),
+// sqrt(21/(32 pi)), sqrt(7/(16 pi)), sqrt(105/(16 pi)).
+constexpr float kSH0 = 0.28209479177387814f;
+constexpr float kSH1 = 0.48860251190291992f;
+constexpr float kSH2a = 1.0925484305920792f;
+constexpr float kSH2b = 0.31539156525252005f;
+constexpr float kSH2c = 0.54627421529603959f;
+constexpr float kSH3a = 0.59004358992664352f;
+constexpr float kSH3b = 2.8906114426405538f;
+constexpr float kSH3c = 0.45704579946446572f;
+constexpr float kSH3d = 0.37317633259011546f;
+constexpr float kSH3e = 1.4453057213202769f;
+
+__device__ __forceinline__ void sh_eval(float x, float y, float z, int deg, float Y[16]) {
+    Y[0] = kSH0;
+    if (deg < 1) return;
+    Y[1] = -kSH1 * y;
+    Y[2] = kSH1 * z;
+    Y[3] = -kSH1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kSH2a * x * y;
+    Y[5] = -kSH2a * y * z;
+    Y[6] = kSH2b * (2.f * zz - xx - yy);
+    Y[7] = -kSH2a * x * z;
+    Y[8] = kSH2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -kSH3a * y * (3.f * xx - yy);
+    Y[10] = kSH3b * x * y * z;
+    Y[11] = -kSH3c * y * (4.f * zz - xx - yy);
+    Y[12] = kSH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -kSH3c * x * (4.f * zz - xx - yy);
+    Y[14] = kSH3e * z * (xx - yy);
+    Y[15] = -kSH3a * x * (xx - 3.f * yy);
+}
+
+// d(sum_k w_k Y_k)/d(x, y, z) for a weight vector w.
+__device__ __forceinline__ void sh_grad(float x, float y, float z, int deg, const float w[16],
+                                        float g[3]) {
+    g[0] = g[1] = g[2] = 0.f;
+    if (deg < 1) return;
+    g[1] += -kSH1 * w[1];
+    g[2] += kSH1 * w[2];
+    g[0] += -kSH1 * w[3];
+    if (deg < 2) return;
+    g[0] += kSH2a * y * w[4];
+    g[1] += kSH2a * x * w[4];
+    g[1] += -kSH2a * z * w[5];
+    g[2] += -kSH2a * y * w[5];
+    g[0] += -2.f * kSH2b * x * w[6];
+    g[1] += -2.f * kSH2b * y * w[6];
+    g[2] += 4.f * kSH2b * z * w[6];
+    g[0] += -kSH2a * z * w[7];
+    g[2] += -kSH2a * x * w[7];
+    g[0] += 2.f * kSH2c * x * w[8];
+    g[1] += -2.f * kSH2c * y * w[8];
+    if (deg < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += -kSH3a * 6.f * x * y * w[9];
+    g[1] += -kSH3a * 3.f * (xx - yy) * w[9];
+    g[0] += kSH3b * y * z * w[10];
+    g[1] += kSH3b * x * z * w[10];
+    g[2] += kSH3b * x * y * w[10];
+    g[0] += kSH3c * 2.f * x * y * w[11];
+    g[1] += -kSH3c * (4.f * zz - xx - 3.f * yy) * w[11];
+    g[2] += -kSH3c * 8.f * y * z * w[11];
+    g[0] += -kSH3d * 6.f * x * z * w[12];
+    g[1] += -kSH3d * 6.f * y * z * w[12];
+    g[2] += kSH3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+    g[0] += -kSH3c * (4.f * zz - 3.f * xx - yy) * w[13];
+    g[1] += kSH3c * 2.f * x * y * w[13];
+    g[2] += -kSH3c * 8.f * x * z * w[13];
+    g[0] += kSH3e * 2.f * x * z * w[14];
+    g[1] += -kSH3e * 2.f * y * z * w[14];
+    g[2] += kSH3e * (xx - yy) * w[14];
+    g[0] += -kSH3a * 3.f * (xx - yy) * w[15];
+    g[1] += kSH3a * 6.f * x * y * w[15];
+}
+
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Geometry shared by the forward and the backward setup.
+struct Setup {
+    bool valid;
+    float o, rho_c;
+    float s[3];
+    float q[4];        // normalised (w, x, y, z)
+    float qnorm;
+    float R[3][3];
+    V3 A[3];           // rows of M_rot R diag(s): the xyz part of (M T) rows 1..3
+    float mu[3];       // view-space mean (the w column of M T)
+    float dir[3];
+    float dist;
+};
+
+__device__ __forceinline__ void setup_geometry(const float *__restrict__ means,
+                                               const float *__restrict__ log_scales,
+                                               const float *__restrict__ quats,
+                                               const float *__restrict__ logits, int64_t i,
+                                               const CamArgs &cam, const ParamArgs &prm,
+                                               Setup &S) {
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const float l = logits[i];
+    // o = sigmoid(logit); rho_c = 2 ln(o / tau_alpha) = -2 (ln(1 + e^{-l}) + ln tau_alpha).
+    S.o = 1.f / (1.f + __expf(-l));
+    S.rho_c = -2.f * (log1pf(__expf(-l)) + __logf(prm.tau_alpha));
+    for (int k = 0; k < 3; ++k) S.s[k] = __expf(log_scales[3 * i + k]);
+    const float4 qr = reinterpret_cast<const float4 *>(quats)[i];
+    S.qnorm = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+    const float inv = 1.f / S.qnorm;
+    const float w = qr.x * inv, x = qr.y * inv, y = qr.z * inv, z = qr.w * inv;
+    S.q[0] = w; S.q[1] = x; S.q[2] = y; S.q[3] = z;
+    S.R[0][0] = 1.f - 2.f * (y * y + z * z); S.R[0][1] = 2.f * (x * y - w * z); S.R[0][2] = 2.f * (x * z + w * y);
+    S.R[1][0] = 2.f * (x * y + w * z); S.R[1][1] = 1.f - 2.f * (x * x + z * z); S.R[1][2] = 2.f * (y * z - w * x);
+    S.R[2][0] = 2.f * (x * z - w * y); S.R[2][1] = 2.f * (y * z + w * x); S.R[2][2] = 1.f - 2.f * (x * x + y * y);
+    // A = M_rot R diag(s); mu_view = M_rot mu + t.
+    for (int r = 0; r < 3; ++r) {
+        float a[3];
+        for (int c = 0; c < 3; ++c)
+            a[c] = (cam.M[4 * r + 0] * S.R[0][c] + cam.M[4 * r + 1] * S.R[1][c] + cam.M[4 * r + 2] * S.R[2][c]) * S.s[c];
+        S.A[r] = v3(a[0], a[1], a[2]);
+        S.mu[r] = cam.M[4 * r + 0] * mx + cam.M[4 * r + 1] * my + cam.M[4 * r + 2] * mz + cam.M[4 * r + 3];
+    }
+    // Cull: rho_c <= 0, or the cutoff ellipsoid reaches z <= z_near.
+    const float e2 = dot(S.A[2], S.A[2]);
+    S.valid = (S.rho_c > 0.f) && (S.mu[2] - sqrtf(S.rho_c * e2) > cam.z_near);
+    const float vx = mx - cam.centre[0], vy = my - cam.centre[1], vz = mz - cam.centre[2];
+    S.dist = sqrtf(vx * vx + vy * vy + vz * vz);
+    const float id = S.dist > 0.f ? 1.f / S.dist : 0.f;
+    S.dir[0] = vx * id; S.dir[1] = vy * id; S.dir[2] = vz * id;
+}
+
+// The expansion vectors of the Pluecker moment m and direction d about the
+// record centre (xc, yc): m = M0 + x' Mx + y' My, d = D0 + x' Dx + y' Dy.
+// a and b are the splat-space planes of the centre pixel's ray,
+// a = T'_1 - xc T'_4, b = T'_2 - yc T'_4 (Sec. 3.2, Eq. (9)), written as
+// fx (MT)_1 + (cx - xc)(MT)_3 to avoid cancelling large terms.
+struct Expansion {
+    V3 a, b, r;          // xyz parts of a, b and T'_4
+    float aw, bw, rw;    // homogeneous parts
+    V3 M0, Mx, My, D0, Dx, Dy;
+};
+
+__device__ __forceinline__ void make_expansion(const Setup &S, const CamArgs &cam, float xc,
+                                               float yc, Expansion &E) {
+    const float ox = cam.cx - xc, oy = cam.cy - yc;
+    E.a = cam.fx * S.A[0] + ox * S.A[2];
+    E.aw = cam.fx * S.mu[0] + ox * S.mu[2];
+    E.b = cam.fy * S.A[1] + oy * S.A[2];
+    E.bw = cam.fy * S.mu[1] + oy * S.mu[2];
+    E.r = S.A[2];
+    E.rw = S.mu[2];
+    // m = a^0 b - b^0 a (the moment, (p^{01}, p^{02}, p^{03})), d = a x b.
+    E.M0 = E.aw * E.b - E.bw * E.a;
+    E.Mx = E.bw * E.r - E.rw * E.b;
+    E.My = E.rw * E.a - E.aw * E.r;
+    E.D0 = cross(E.a, E.b);
+    E.Dx = cross(E.b, E.r);
+    E.Dy = cross(E.r, E.a);
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// K1: forward setup.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_kernel(PreArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
+    uint32_t count = 0;
+    unsigned long long box_pixels = 0;
+    if (i < a.n) {
+        Setup S;
+        setup_geometry(a.means, a.log_scales, a.quats, a.logits, i, a.cam, a.prm, S);
+        uint2 rect = make_uint2(1u, 0u);
+        float4 rec[kRecF4];
+        for (int k = 0; k < kRecF4; ++k) rec[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (S.valid) {
+            // Tight bounding box (Sec. 3.2). With u = fx (MT)_1, w = (MT)_3 and the
+            // form B(x, y) = rho_c x_xyz . y_xyz - x_w y_w (the dual quadric
+            // diag(rho_c, rho_c, rho_c, -1) mapped by T'), p = B(u, w)/B(w, w) + cx
+            // and h^2 = (B(u, w)^2 - B(u, u) B(w, w)) / B(w, w)^2, whose numerator
+            // expands to rho_c (|w_w U - u_w W|^2 - rho_c |U x W|^2); this avoids
+            // the cancellation of p^2 - <f, T'_i . T'_i> in single precision.
+            const float rc = S.rho_c;
+            const float sden = rc * dot(S.A[2], S.A[2]) - S.mu[2] * S.mu[2]; // < 0
+            float pc[2], hc[2];
+            for (int ax = 0; ax < 2; ++ax) {
+                const float f = ax == 0 ? a.cam.fx : a.cam.fy;
+                const float c = ax == 0 ? a.cam.cx : a.cam.cy;
+                const V3 U = S.A[ax];
+                const float uw = S.mu[ax];
+                pc[ax] = f * (rc * dot(U, S.A[2]) - uw * S.mu[2]) / sden + c;
+                const V3 t = S.mu[2] * U - uw * S.A[2];
+                const V3 cr = cross(U, S.A[2]);
+                const float num = rc * (dot(t, t) - rc * dot(cr, cr));
+                hc[ax] = fabsf(f) * sqrtf(fmaxf(num, 0.f)) / fabsf(sden);
+            }
+            // Covered pixel rectangle, widened by a small margin against rounding
+            // (a wider box only adds work; the per-pixel test decides).
+            const float lim[2] = {(float)(a.cam.width - 1), (float)(a.cam.height - 1)};
+            float lo[2], hi[2];
+            bool ok = true;
+            for (int ax = 0; ax < 2; ++ax) {
+                const float m = 1e-3f * hc[ax] + 1e-2f;
+                lo[ax] = fmaxf(ceilf(pc[ax] - hc[ax] - 0.5f - m), 0.f);
+                hi[ax] = fminf(floorf(pc[ax] + hc[ax] - 0.5f + m), lim[ax]);
+                ok = ok && (lo[ax] <= hi[ax]);
+            }
+            if (ok) {
+                box_pixels = (unsigned long long)(hi[0] - lo[0] + 1.f) * (unsigned long long)(hi[1] - lo[1] + 1.f);
+                const uint32_t tx0 = (uint32_t)lo[0] / a.tiles.tile_w, tx1 = (uint32_t)hi[0] / a.tiles.tile_w;
+                const uint32_t ty0 = (uint32_t)lo[1] / a.tiles.tile_h, ty1 = (uint32_t)hi[1] / a.tiles.tile_h;
+                rect = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+                count = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+                // Record: quadratic coefficients about the box centre.
+                const float xc = pc[0], yc = pc[1];
+                Expansion E;
+                make_expansion(S, a.cam, xc, yc, E);
+                float n[6], d[6], zq[6];
+                n[0] = dot(E.M0, E.M0); n[1] = 2.f * dot(E.M0, E.Mx); n[2] = 2.f * dot(E.M0, E.My);
+                n[3] = dot(E.Mx, E.Mx); n[4] = 2.f * dot(E.Mx, E.My); n[5] = dot(E.My, E.My);
+                d[0] = dot(E.D0, E.D0); d[1] = 2.f * dot(E.D0, E.Dx); d[2] = 2.f * dot(E.D0, E.Dy);
+                d[3] = dot(E.Dx, E.Dx); d[4] = 2.f * dot(E.Dx, E.Dy); d[5] = dot(E.Dy, E.Dy);
+                // z D = T'_4,xyz . (d x m) + T'_4,w D, expanded in (x', y').
+                const V3 C0 = cross(E.D0, E.M0);
+                const V3 C1 = cross(E.D0, E.Mx) + cross(E.Dx, E.M0);
+                const V3 C2 = cross(E.D0, E.My) + cross(E.Dy, E.M0);
+                const V3 C3 = cross(E.Dx, E.Mx);
+                const V3 C4 = cross(E.Dx, E.My) + cross(E.Dy, E.Mx);
+                const V3 C5 = cross(E.Dy, E.My);
+                zq[0] = dot(E.r, C0) + E.rw * d[0];
+                zq[1] = dot(E.r, C1) + E.rw * d[1];
+                zq[2] = dot(E.r, C2) + E.rw * d[2];
+                zq[3] = dot(E.r, C3) + E.rw * d[3];
+                zq[4] = dot(E.r, C4) + E.rw * d[4];
+                zq[5] = dot(E.r, C5) + E.rw * d[5];
+                const float hl = 0.72134752044448170f; // log2(e) / 2
+                float q[6];
+                for (int k = 0; k < 6; ++k) q[k] = hl * (rc * d[k] - n[k]);
+                // Colour (Sec. 3.1, identical to 3DGS): max(0, 0.5 + sum Y_k sh_k).
+                const int nc = (a.sh_degree + 1) * (a.sh_degree + 1);
+                float Y[16];
+                sh_eval(S.dir[0], S.dir[1], S.dir[2], a.sh_degree, Y);
+                const float *sh = a.sh + i * nc * 3;
+                float rgb[3] = {0.5f, 0.5f, 0.5f};
+                for (int k = 0; k < nc; ++k) {
+                    rgb[0] += Y[k] * sh[3 * k + 0];
+                    rgb[1] += Y[k] * sh[3 * k + 1];
+                    rgb[2] += Y[k] * sh[3 * k + 2];
+                }
+                rec[0] = make_float4(xc, yc, q[0], q[1]);
+                rec[1] = make_float4(q[2], q[3], q[4], q[5]);
+                rec[2] = make_float4(d[0], d[1], d[2], d[3]);
+                rec[3] = make_float4(d[4], d[5], zq[0], zq[1]);
+                rec[4] = make_float4(zq[2], zq[3], zq[4], zq[5]);
+                rec[5] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), rc);
+            }
+        }
+        float4 *dst = a.rec + i * kRecF4;
+        for (int k = 0; k < kRecF4; ++k) dst[k] = rec[k];
+        a.rect[i] = rect;
+        a.count[i] = count;
+    }
+    // Block sum of counts for the instance scan.
+    __shared__ uint32_t warp_sums[kPreThreads / 32];
+    __shared__ unsigned long long warp_px[kPreThreads / 32];
+    uint32_t v = count;
+    unsigned long long bp = box_pixels;
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        bp += __shfl_xor_sync(0xffffffffu, bp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        warp_sums[threadIdx.x >> 5] = v;
+        warp_px[threadIdx.x >> 5] = bp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        unsigned long long px = 0;
+        for (int w = 0; w < kPreThreads / 32; ++w) {
+            s += warp_sums[w];
+            px += warp_px[w];
+        }
+        a.block_sums[blockIdx.x] = s;
+        if (px) atomicAdd(a.stats + kStatBoxPairs, px);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K8: backward setup. acc holds per Gaussian 16 floats accumulated by the
+// blend adjoint: dL/d(N coefficients)[6], dL/d(D coefficients)[6],
+// sum(dL/dalpha * alpha) and dL/d(rgb)[3]. N = ||m||^2 and D = ||d||^2 are
+// the quadratics of the Pluecker moment and direction (Eq. (13) gives
+// rho^2 = N / D); alpha = o e^{-N/(2D)}, so dL/do = sum(dL/dalpha alpha)/o.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_backward_kernel(PreBwdArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
+    if (i >= a.n) return;
+    const int nc = (a.sh_degree + 1) * (a.sh_degree + 1);
+    float *gmu = a.g_means + 3 * i, *gls = a.g_log_scales + 3 * i, *gq = a.g_quats + 4 * i;
+    float *gsh = a.g_sh + i * nc * 3;
+    Setup S;
+    setup_geometry(a.means, a.log_scales, a.quats, a.logits, i, a.cam, a.prm, S);
+    const uint2 rect = a.rect[i];
+    const bool active = S.valid && ((rect.x & 0xffffu) <= (rect.x >> 16));
+    if (!active) {
+        for (int k = 0; k < 3; ++k) { gmu[k] = 0.f; gls[k] = 0.f; }
+        for (int k = 0; k < 4; ++k) gq[k] = 0.f;
+        a.g_logits[i] = 0.f;
+        for (int k = 0; k < nc * 3; ++k) gsh[k] = 0.f;
+        return;
+    }
+    const float4 *acc4 = reinterpret_cast<const float4 *>(a.acc + 16 * i);
+    const float4 A0 = acc4[0], A1 = acc4[1], A2 = acc4[2], A3 = acc4[3];
+    const float gN[6] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y};
+    const float gD[6] = {A1.z, A1.w, A2.x, A2.y, A2.z, A2.w};
+    const float g_aa = A3.x;
+    const float gc[3] = {A3.y, A3.z, A3.w};
+
+    const float4 r0 = a.rec[i * kRecF4];
+    Expansion E;
+    make_expansion(S, a.cam, r0.x, r0.y, E);
+    // N = n0 + n1 x' + ..., n0 = M0.M0, n1 = 2 M0.Mx, n2 = 2 M0.My, n3 = Mx.Mx,
+    // n4 = 2 Mx.My, n5 = My.My; the same for D with the d vectors.
+    const V3 dM0 = 2.f * (gN[0] * E.M0 + gN[1] * E.Mx + gN[2] * E.My);
+    const V3 dMx = 2.f * (gN[1] * E.M0 + gN[3] * E.Mx + gN[4] * E.My);
+    const V3 dMy = 2.f * (gN[2] * E.M0 + gN[4] * E.Mx + gN[5] * E.My);
+    const V3 dD0 = 2.f * (gD[0] * E.D0 + gD[1] * E.Dx + gD[2] * E.Dy);
+    const V3 dDx = 2.f * (gD[1] * E.D0 + gD[3] * E.Dx + gD[4] * E.Dy);
+    const V3 dDy = 2.f * (gD[2] * E.D0 + gD[4] * E.Dx + gD[5] * E.Dy);
+    V3 da = v3(0.f, 0.f, 0.f), db = da, dr = da;
+    float daw = 0.f, dbw = 0.f, drw = 0.f;
+    // M0 = aw b - bw a
+    daw += dot(dM0, E.b); db = db + E.aw * dM0; dbw -= dot(dM0, E.a); da = da - E.bw * dM0;
+    // Mx = bw r - rw b
+    dbw += dot(dMx, E.r); dr = dr + E.bw * dMx; drw -= dot(dMx, E.b); db = db - E.rw * dMx;
+    // My = rw a - aw r
+    drw += dot(dMy, E.a); da = da + E.rw * dMy; daw -= dot(dMy, E.r); dr = dr - E.aw * dMy;
+    // D0 = a x b, Dx = b x r, Dy = r x a
+    da = da + cross(E.b, dD0); db = db + cross(dD0, E.a);
+    db = db + cross(E.r, dDx); dr = dr + cross(dDx, E.b);
+    dr = dr + cross(E.a, dDy); da = da + cross(dDy, E.r);
+    // a = fx (MT)_1 + (cx - xc)(MT)_3, b = fy (MT)_2 + (cy - yc)(MT)_3, r = (MT)_3.
+    const float ox = a.cam.cx - r0.x, oy = a.cam.cy - r0.y;
+    V3 dA[3];
+    float dmuv[3];
+    dA[0] = a.cam.fx * da;           dmuv[0] = a.cam.fx * daw;
+    dA[1] = a.cam.fy * db;           dmuv[1] = a.cam.fy * dbw;
+    dA[2] = ox * da + oy * db + dr;  dmuv[2] = ox * daw + oy * dbw + drw;
+    // A = M_rot B with B = R diag(s); mu_view = M_rot mu + t.
+    float dB[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const float c0 = a.cam.M[0 + k], c1 = a.cam.M[4 + k], c2 = a.cam.M[8 + k];
+        dB[k][0] = c0 * dA[0].x + c1 * dA[1].x + c2 * dA[2].x;
+        dB[k][1] = c0 * dA[0].y + c1 * dA[1].y + c2 * dA[2].y;
+        dB[k][2] = c0 * dA[0].z + c1 * dA[1].z + c2 * dA[2].z;
+        gmu[k] = c0 * dmuv[0] + c1 * dmuv[1] + c2 * dmuv[2];
+    }
+    float dR[3][3];
+    for (int j = 0; j < 3; ++j) {
+        float ds = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            ds += dB[k][j] * S.R[k][j];
+            dR[k][j] = dB[k][j] * S.s[j];
+        }
+        gls[j] = ds * S.s[j];
+    }
+    const float w = S.q[0], x = S.q[1], y = S.q[2], z = S.q[3];
+    float dq[4];
+    dq[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    dq[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                   z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+    dq[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                   w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+    dq[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                   y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float pdot = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+    const float iq = 1.f / S.qnorm;
+    for (int k = 0; k < 4; ++k) gq[k] = (dq[k] - S.q[k] * pdot) * iq;
+    // o = sigmoid(l): dL/dl = (sum dL/dalpha alpha / o) o (1 - o).
+    a.g_logits[i] = g_aa * (1.f - S.o);
+    // Colour: channels clamped at zero pass no gradient.
+    float Y[16];
+    sh_eval(S.dir[0], S.dir[1], S.dir[2], a.sh_degree, Y);
+    const float *sh = a.sh + i * nc * 3;
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < nc; ++k)
+        for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * sh[3 * k + ch];
+    float gce[3];
+    for (int ch = 0; ch < 3; ++ch) gce[ch] = raw[ch] > 0.f ? gc[ch] : 0.f;
+    float wdir[16];
+    for (int k = 0; k < 16; ++k) wdir[k] = 0.f;
+    for (int k = 0; k < nc; ++k) {
+        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = gce[ch] * Y[k];
+        wdir[k] = gce[0] * sh[3 * k] + gce[1] * sh[3 * k + 1] + gce[2] * sh[3 * k + 2];
+    }
+    float gd[3];
+    sh_grad(S.dir[0], S.dir[1], S.dir[2], a.sh_degree, wdir, gd);
+    if (S.dist > 0.f) {
+        const float pd = gd[0] * S.dir[0] + gd[1] * S.dir[1] + gd[2] * S.dir[2];
+        const float id = 1.f / S.dist;
+        for (int k = 0; k < 3; ++k) gmu[k] += (gd[k] - S.dir[k] * pd) * id;
+    }
+}
+
+} // namespace htgs

@@ -1,0 +1,135 @@
+"""Workspace management and the torch.autograd.Function over the C ABI.
+
+PyTorch provides device memory and the stream; every step of the render and
+of its adjoint runs in libhtgs (hand-written sm_103a kernels).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import binding as B
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@dataclasses.dataclass
+class GaussianTensors:
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "GaussianTensors":
+        def t(a):
+            return torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return GaussianTensors(t(scene.means), t(scene.log_scales), t(scene.quats),
+                               t(scene.opacity_logits), t(scene.sh), int(scene.sh_degree))
+
+    def c_struct(self) -> B.Gaussians:
+        return B.c_gaussians(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh,
+                             self.sh_degree)
+
+    def tensors(self):
+        return [getattr(self, f) for f in FIELDS]
+
+
+class Renderer:
+    """Owns the caller-side buffers of one (camera, K, launch) configuration:
+    the workspace (binning, sort, records, gradient accumulators) and the
+    per-pixel state saved for the backward."""
+
+    def __init__(self, camera, params, n, launch=None, capacity=None, device="cuda"):
+        self.camera = camera
+        self.params = params
+        self.n = int(n)
+        self.launch = launch if launch is not None else B.c_launch()
+        self.device = torch.device(device)
+        self.capacity = int(capacity) if capacity else max(8 * self.n, 1 << 16)
+        self.workspace = None
+        self.saved = None
+        self._alloc()
+
+    def _alloc(self):
+        fwd, saved = B.htgs_workspace_size(self.n, self.camera, self.params, self.launch, self.capacity)
+        # 256-byte aligned by the caching allocator.
+        self.workspace = torch.empty(max(fwd, 256), dtype=torch.uint8, device=self.device)
+        self.saved = torch.empty(max(saved // 4, 1), dtype=torch.float32, device=self.device)
+
+    def grow(self, needed: int):
+        self.capacity = max(int(needed * 1.25) + 1024, self.capacity)
+        self._alloc()
+
+    def image_buffer(self):
+        return torch.empty((self.camera.height, self.camera.width, 3), dtype=torch.float32,
+                           device=self.device)
+
+    def forward(self, g: GaussianTensors, image=None, save=True, check=True, stream=None):
+        """Renders into `image` (allocated when None). With check=True the
+        stream is synchronised once to read the device status; on an
+        instance overflow the workspace grows and the render is repeated."""
+        if image is None:
+            image = self.image_buffer()
+        cg = g.c_struct()
+        for _ in range(4):
+            st = B.htgs_render(cg, self.camera, self.params, self.launch, self.workspace, self.capacity,
+                               self.saved if save else None, image, stream)
+            B._check(st, "htgs_render")
+            if not check:
+                return image
+            dev_status, inst = B.htgs_get_error(self.workspace, stream)
+            if dev_status == B.HTGS_ERR_OVERFLOW:
+                self.grow(inst)
+                continue
+            B._check(dev_status, "htgs_render (device)")
+            self.last_instances = inst
+            return image
+        raise B.HTGSError(B.HTGS_ERR_OVERFLOW, "htgs_render")
+
+    def backward(self, g: GaussianTensors, dl_dimage: torch.Tensor, grads=None, stream=None):
+        dl = dl_dimage.contiguous()
+        if dl.dtype != torch.float32 or tuple(dl.shape) != (self.camera.height, self.camera.width, 3):
+            raise ValueError("dl_dimage must be float32 of shape (H, W, 3)")
+        if grads is None:
+            grads = {f: torch.empty_like(getattr(g, f)) for f in FIELDS}
+        cgrad = B.GaussiansGrad(*[B._ptr(grads[f]).value for f in FIELDS])
+        st = B.htgs_render_backward(g.c_struct(), self.camera, self.params, self.launch, self.workspace,
+                                    self.capacity, self.saved, dl, cgrad, stream)
+        B._check(st, "htgs_render_backward")
+        return grads
+
+    def status(self, stream=None):
+        return B.htgs_get_error(self.workspace, stream)
+
+
+class RenderFunction(torch.autograd.Function):
+    """image = render(means, log_scales, quats, opacity_logits, sh); the
+    backward calls htgs_render_backward on the saved per-pixel state."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, sh_degree: int, means, log_scales, quats, opacity_logits, sh):
+        g = GaussianTensors(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
+                            opacity_logits.contiguous(), sh.contiguous(), sh_degree)
+        image = renderer.forward(g, save=True, check=True)
+        ctx.renderer = renderer
+        ctx.g = g
+        return image
+
+    @staticmethod
+    def backward(ctx, dl_dimage):
+        grads = ctx.renderer.backward(ctx.g, dl_dimage)
+        return (None, None) + tuple(grads[f] for f in FIELDS)
+
+
+def render(g: GaussianTensors, renderer: Renderer):
+    """Differentiable render of one view (hybrid transparency, Eq. (15))."""
+    return RenderFunction.apply(renderer, g.sh_degree, g.means, g.log_scales, g.quats,
+                                g.opacity_logits, g.sh)

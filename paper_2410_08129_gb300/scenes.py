@@ -70,6 +70,13 @@ class Camera:
     width: int
     height: int
 
+    def rounded(self) -> "Camera":
+        """The camera with every parameter rounded to float32, the precision
+        the C ABI takes it in (so that a float64 consumer sees the same camera)."""
+        f = lambda v: float(np.float32(v))
+        return Camera(self.world_to_cam.astype(np.float32).astype(np.float64), f(self.fx), f(self.fy),
+                      f(self.cx), f(self.cy), f(self.z_near), self.width, self.height)
+
     def crop(self, x0: int, y0: int, w: int, h: int) -> "Camera":
         """The same camera restricted to pixels [x0, x0+w) x [y0, y0+h)."""
         return Camera(self.world_to_cam.copy(), self.fx, self.fy,

@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/htgs.h declares; host-only entry points validate arguments."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2410_08129_gb300 import build as build_mod
+from paper_2410_08129_gb300 import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(htgs_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return build_mod.build()
+
+
+def test_every_declared_symbol_is_exported(lib_path):
+    declared = _declared()
+    assert len(declared) >= 7
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (htgs_\w+)", out))
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_host_entry_points_work(lib_path):
+    from paper_2410_08129_gb300 import binding as B
+    L = B.lib()
+    for n in _declared():
+        assert hasattr(L, n)
+    _, cam, prm, tile = scenes.config1()
+    fwd, saved = B.htgs_workspace_size(256, cam, prm, B.c_launch(tile), 1 << 16)
+    assert fwd % 256 == 0 and saved == (7 + prm.K) * 64 * 64 * 4
+    lay = B.htgs_workspace_layout(256, cam, prm, B.c_launch(tile), 1 << 16)
+    assert lay.n_tiles == 16 and lay.tiles_x == 4 and lay.tile_bits == 4
+    assert B.htgs_status_string(B.HTGS_ERR_OVERFLOW) != B.htgs_status_string(B.HTGS_OK)
+
+
+@pytest.mark.parametrize("bad", ["K", "capacity", "tile", "n", "alpha_max", "size"])
+def test_host_side_argument_checks(lib_path, bad):
+    from paper_2410_08129_gb300 import binding as B
+    _, cam, prm, tile = scenes.config1()
+    n, cap, launch = 256, 1 << 16, B.c_launch(tile)
+    if bad == "K":
+        prm = scenes.Params(K=33)
+        expect = B.HTGS_ERR_NOT_SUPPORTED
+    elif bad == "capacity":
+        cap = 1 << 31
+        expect = B.HTGS_ERR_INVALID_ARG
+    elif bad == "tile":
+        launch = B.c_launch((12, 12))
+        expect = B.HTGS_ERR_NOT_SUPPORTED
+    elif bad == "n":
+        n = -1
+        expect = B.HTGS_ERR_INVALID_ARG
+    elif bad == "alpha_max":
+        prm = scenes.Params(alpha_max=1.0)
+        expect = B.HTGS_ERR_INVALID_ARG
+    else:
+        cam = scenes.identity_camera(0, 10, 10.0)
+        expect = B.HTGS_ERR_INVALID_ARG
+    with pytest.raises(B.HTGSError) as e:
+        B.htgs_workspace_size(n, cam, prm, launch, cap)
+    assert e.value.status == expect
+
+
+def test_oracle_is_not_linked_into_the_library(lib_path):
+    out = subprocess.run(["nm", "-D", lib_path], capture_output=True, text=True, check=True).stdout
+    assert "og_" not in out
+    deps = subprocess.run(["readelf", "-d", lib_path], capture_output=True, text=True, check=True).stdout
+    assert "htgs_oracle" not in deps

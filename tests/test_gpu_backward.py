@@ -1,0 +1,92 @@
+"""GPU parity of the adjoint (Sec. 3.3) through the C ABI: gradients of the
+means, log-scales, quaternions, opacity logits and SH coefficients against
+the FP64 oracle's analytic gradient (itself pinned by FP64 central
+differences in test_oracle_backward.py)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_08129_gb300 import binding as B
+from paper_2410_08129_gb300 import scenes
+from paper_2410_08129_gb300.renderer import FIELDS, GaussianTensors, Renderer, render
+from tests.gpu_util import assert_grad_close, grads_to_numpy
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_grads(scene, cam, prm, dl, tile=(16, 16), ppt=0):
+    g = GaussianTensors.from_scene(scene)
+    r = Renderer(cam, prm, scene.n, launch=B.c_launch(tile, ppt))
+    r.forward(g)
+    grads = r.backward(g, torch.as_tensor(dl, dtype=torch.float32).cuda())
+    torch.cuda.synchronize()
+    return grads_to_numpy(grads), r
+
+
+def _masked_upstream(scene, cam, prm, seed):
+    """Random dL/dimage, zeroed on pixels with a near-decision (their discrete
+    choices may differ between FP32 and FP64, see the oracle's flags)."""
+    _, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    dl = np.random.default_rng(seed).standard_normal((cam.height, cam.width, 3))
+    dl[d["near_decision"] != 0] = 0.0
+    return dl.astype(np.float32), d
+
+
+@pytest.mark.parametrize("degree,K,tile,ppt", [(0, 8, (16, 16), 2), (3, 4, (16, 8), 1), (3, 16, (8, 8), 2),
+                                               (1, 0, (16, 16), 4), (2, 32, (16, 16), 1)])
+def test_small_scene_gradients(degree, K, tile, ppt):
+    """64 Gaussians of the training-step distribution seen through a 32x32
+    crop of the 1200x800 camera (principal point shifted)."""
+    scene = scenes.small_box_scene(64, seed=2, sh_degree=degree)
+    scene.sh[:, 1:, :] *= np.float32(6.0)
+    cam = scenes.identity_camera(1200, 800, 1200.0).crop(584, 384, 32, 32).rounded()
+    prm = scenes.Params(K=K, bg=(0.1, 0.2, 0.3))
+    # Concentrate the Gaussians on the crop so that every one of them matters.
+    scene.means[:, :2] *= np.float32(0.04)
+    dl, d = _masked_upstream(scene, cam, prm, seed=degree + K)
+    ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl.astype(np.float64))
+    got, _ = _gpu_grads(scene, cam, prm, dl, tile, ppt)
+    rep = assert_grad_close(got, ref)
+    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()}, "masked", (d["near_decision"] != 0).mean())
+
+
+def test_autograd_function_matches_direct_call():
+    scene = scenes.small_box_scene(40, seed=9, sh_degree=1)
+    cam = scenes.identity_camera(48, 40, 50.0).rounded()
+    prm = scenes.Params(K=4)
+    g = GaussianTensors.from_scene(scene)
+    for t in g.tensors():
+        t.requires_grad_(True)
+    r = Renderer(cam, prm, scene.n)
+    img = render(g, r)
+    dl = torch.randn_like(img)
+    (img * dl).sum().backward()
+    r2 = Renderer(cam, prm, scene.n)
+    g2 = GaussianTensors.from_scene(scene)
+    r2.forward(g2)
+    direct = r2.backward(g2, dl)
+    for f in FIELDS:
+        torch.testing.assert_close(getattr(g, f).grad, direct[f], rtol=1e-5, atol=1e-6)
+
+
+def test_training_step_distribution_crop_gradients():
+    """500k Gaussians of the training-step configuration at 1200x800 with the
+    upstream gradient on a 32x32 window: every Gaussian's gradient equals
+    the oracle's gradient of that window."""
+    scene, target, cam, prm = scenes.config3()
+    cam = cam.rounded()
+    win = (584, 384, 32, 32)
+    x0, y0, w, h = win
+    _, d = oracle.render(scene.astype(np.float64), cam, prm, window=win, diagnostics=True)
+    dl_win = np.random.default_rng(3).standard_normal((h, w, 3))
+    dl_win[d["near_decision"] != 0] = 0.0
+    dl = np.zeros((cam.height, cam.width, 3), np.float32)
+    dl[y0:y0 + h, x0:x0 + w] = dl_win
+    ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl_win, window=win)
+    got, r = _gpu_grads(scene, cam, prm, dl)
+    touched = np.abs(ref["opacity_logits"]) > 0
+    assert touched.sum() > 1000
+    rep = assert_grad_close(got, ref)
+    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()}, "touched", int(touched.sum()),
+          "masked", float((d["near_decision"] != 0).mean()), "instances", r.last_instances)

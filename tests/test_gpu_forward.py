@@ -1,0 +1,170 @@
+"""GPU parity of the forward path through the C ABI against the FP64 oracle
+(Sec. 3.2-3.3): image, per-pixel core ids, tile binning, launch-shape
+invariance, determinism, edge cases and the overflow protocol."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_08129_gb300 import binding as B
+from paper_2410_08129_gb300 import scenes
+from paper_2410_08129_gb300.renderer import GaussianTensors, Renderer
+from tests.gpu_util import (IMAGE_TOL, compare_images, gpu_render, saved_planes, workspace_view)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    scene, cam, prm, tile = scenes.config1()
+    cam = cam.rounded()
+    img, r, g = gpu_render(scene, cam, prm, tile=tile)
+    ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    return scene, cam, prm, tile, img, r, g, ref, d
+
+
+def test_config1_image_parity(cfg1):
+    scene, cam, prm, tile, img, r, g, ref, d = cfg1
+    e_ok, amb_frac, e_amb = compare_images(img, ref, d["ambiguous"])
+    print(f"config1: max err {e_ok:.3e} on unambiguous pixels, ambiguous {amb_frac:.4f} (max err {e_amb:.3e})")
+    assert np.isfinite(img).all()
+    assert e_ok <= IMAGE_TOL
+    assert amb_frac <= 0.01
+
+
+def test_config1_core_ids_match(cfg1):
+    """The K-core (ids in depth order) is integer work: identical on every
+    pixel without a near-decision."""
+    scene, cam, prm, tile, img, r, g, ref, d = cfg1
+    sv = saved_planes(r, cam, prm.K)
+    ok = d["ambiguous"] == 0
+    np.testing.assert_array_equal(sv["n_core"][ok], d["n_core"][ok])
+    np.testing.assert_array_equal(sv["core_gid"][ok], d["core_gid"][ok])
+    # T_core per pixel (FP32 vs FP64)
+    assert np.abs(sv["T_core"][ok] - d["T_core"][ok]).max() <= 1e-5
+
+
+def test_config1_binning_matches_oracle(cfg1):
+    """Tile lists: GPU sorted lists equal the oracle's binning of the GPU's
+    own rectangles (bit-exact), and every oracle-covered pixel lies in a
+    tile the GPU emitted for that Gaussian."""
+    scene, cam, prm, tile, img, r, g, ref, d = cfg1
+    lay = B.htgs_workspace_layout(scene.n, cam, prm, r.launch, r.capacity)
+    n = scene.n
+    rect = workspace_view(r, lay.rect, 2 * n, torch.int32).view(n, 2).cpu().numpy().view(np.uint32)
+    tx0, tx1 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16
+    ty0, ty1 = rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
+    tw, th = tile
+    empty = tx0 > tx1
+    prect = np.stack([tx0 * tw, (tx1 + 1) * tw - 1, ty0 * th, (ty1 + 1) * th - 1], 1).astype(np.int64)
+    prect[:, 1] = np.minimum(prect[:, 1], cam.width - 1)
+    prect[:, 3] = np.minimum(prect[:, 3], cam.height - 1)
+    prect[empty] = [0, -1, 0, -1]
+    counts, lists = oracle.bin_tiles(prect, cam.width, cam.height, tw, th)
+    ranges = workspace_view(r, lay.ranges, 2 * lay.n_tiles, torch.int32).view(-1, 2).cpu().numpy()
+    total = int(counts.sum())
+    vals = workspace_view(r, lay.sorted_vals, total, torch.int32).cpu().numpy()
+    assert r.last_instances == total
+    off = 0
+    for t in range(lay.n_tiles):
+        c = int(counts[t])
+        if c:
+            assert ranges[t, 0] == off and ranges[t, 1] == off + c
+        np.testing.assert_array_equal(vals[off:off + c], lists[off:off + c])
+        off += c
+    # Validity: the oracle's covered pixel rectangle lies inside the GPU tiles.
+    sp = oracle.preprocess(scene.astype(np.float64), cam, prm)
+    for gi in np.flatnonzero(sp["valid"]):
+        x0, x1, y0, y1 = sp["rect"][gi]
+        if x0 > x1 or y0 > y1:
+            continue
+        assert not empty[gi]
+        assert tx0[gi] * tw <= x0 and x1 <= (tx1[gi] + 1) * tw - 1
+        assert ty0[gi] * th <= y0 and y1 <= (ty1[gi] + 1) * th - 1
+
+
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((16, 16), 4), ((16, 8), 2), ((8, 8), 1), ((8, 8), 2)])
+def test_launch_shapes_agree(cfg1, tile, ppt):
+    """Tile shape and pixels per thread are tuning knobs: the per-pixel
+    arithmetic and the (gid-ascending) traversal order do not change."""
+    scene, cam, prm, _, img, *_ = cfg1
+    img2, *_ = gpu_render(scene, cam, prm, tile=tile, ppt=ppt)
+    assert np.abs(img2 - img).max() <= 1e-6
+
+
+def test_deterministic(cfg1):
+    scene, cam, prm, tile, img, r, g, *_ = cfg1
+    a = r.forward(g).cpu().numpy()
+    b = r.forward(g).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("K", [0, 1, 8, 16, 32])
+def test_k_values(K):
+    scene = scenes.small_box_scene(300, seed=5, sh_degree=1)
+    scene.log_scales += np.float32(0.4)
+    cam = scenes.identity_camera(80, 56, 70.0).rounded()
+    prm = scenes.Params(K=K, bg=(0.2, 0.3, 0.4))
+    img, r, g = gpu_render(scene, cam, prm)
+    ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    e_ok, amb_frac, e_amb = compare_images(img, ref, d["ambiguous"])
+    print(f"K={K}: err {e_ok:.3e} amb {amb_frac:.4f} ({e_amb:.3e}), frags/px max {d['n_frag'].max()}")
+    assert e_ok <= IMAGE_TOL and amb_frac <= 0.02
+
+
+def test_ragged_image_and_big_splats():
+    """Image sizes that are not tile multiples; splats much larger than a tile."""
+    scene = scenes.small_box_scene(60, seed=6, sh_degree=2)
+    scene.log_scales += np.float32(1.0)
+    cam = scenes.Camera(scenes.look_at((0.1, 0.2, -0.4), (0, 0, 3)), 75.0, 70.0, 50.3, 17.9, 0.2, 101, 37).rounded()
+    prm = scenes.Params(K=4, bg=(1.0, 0.5, 0.0))
+    for tile in [(16, 16), (16, 8), (8, 8)]:
+        img, r, g = gpu_render(scene, cam, prm, tile=tile)
+        ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+        e_ok, amb_frac, _ = compare_images(img, ref, d["ambiguous"])
+        assert e_ok <= IMAGE_TOL and amb_frac <= 0.02, (tile, e_ok, amb_frac)
+
+
+def test_empty_and_culled_scenes():
+    cam = scenes.identity_camera(40, 24, 30.0).rounded()
+    prm = scenes.Params(K=4, bg=(0.25, 0.5, 0.75))
+    empty = scenes.small_box_scene(0, seed=1)
+    img, *_ = gpu_render(empty, cam, prm)
+    assert np.array_equal(img, np.broadcast_to(np.float32(prm.bg), img.shape).astype(np.float64))
+    behind = scenes.small_box_scene(50, seed=2)
+    behind.means[:, 2] = -3.0
+    img, r, _ = gpu_render(behind, cam, prm)
+    assert r.last_instances == 0
+    np.testing.assert_allclose(img, np.broadcast_to(prm.bg, img.shape), atol=1e-7)
+
+
+def test_overflow_is_reported_and_recovered():
+    scene, cam, prm, tile = scenes.config1()
+    cam = cam.rounded()
+    g = GaussianTensors.from_scene(scene)
+    r = Renderer(cam, prm, scene.n, launch=B.c_launch(tile), capacity=16)
+    img = r.image_buffer()
+    st = B.htgs_render(g.c_struct(), cam, prm, r.launch, r.workspace, r.capacity, r.saved, img)
+    assert st == B.HTGS_OK
+    dev, inst = B.htgs_get_error(r.workspace)
+    assert dev == B.HTGS_ERR_OVERFLOW and inst > 16
+    img2 = r.forward(g)           # grows the workspace and re-renders
+    assert r.last_instances == inst
+    ref = oracle.render(scene.astype(np.float64), cam, prm)
+    assert np.abs(img2.cpu().numpy() - ref).max() < 0.05
+
+
+def test_invalid_arguments_rejected():
+    scene, cam, prm, tile = scenes.config1()
+    g = GaussianTensors.from_scene(scene)
+    r = Renderer(cam, prm, scene.n, launch=B.c_launch(tile))
+    img = r.image_buffer()
+    bad = scenes.Params(K=33)
+    with pytest.raises(B.HTGSError):
+        B.htgs_workspace_size(scene.n, cam, bad, r.launch, 100)
+    small = r.workspace[:1024]
+    assert B.htgs_render(g.c_struct(), cam, prm, r.launch, small, r.capacity, None, img) == B.HTGS_ERR_WORKSPACE
+    assert B.htgs_render(g.c_struct(), cam, prm, B.c_launch((32, 32)), r.workspace, r.capacity, None,
+                         img) == B.HTGS_ERR_NOT_SUPPORTED

@@ -1,0 +1,68 @@
+"""GPU parity at the benchmark sizes (1M clustered Gaussians at 1920x1080;
+6M-Gaussian stress scene with flat splats, near-camera splats and opacities
+at the clamp), in the launch configuration the benchmark times. The oracle
+brute-forces every Gaussian for every pixel of small windows."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_08129_gb300 import binding as B
+from paper_2410_08129_gb300 import scenes
+from paper_2410_08129_gb300.renderer import GaussianTensors, Renderer
+from tests.gpu_util import IMAGE_TOL, crop_compare, gpu_render
+
+pytestmark = pytest.mark.gpu
+
+WINDOWS_1080 = [(940, 520, 40, 40), (400, 700, 32, 24), (1500, 200, 24, 32)]
+
+
+@pytest.fixture(scope="module")
+def cfg2_scene():
+    scene, cam, prm = scenes.config2()
+    return scene, cam.rounded()
+
+
+@pytest.mark.parametrize("K", [8, 4, 16])
+def test_config2_windows(cfg2_scene, K):
+    scene, cam = cfg2_scene
+    prm = scenes.Params(K=K)
+    img, r, g = gpu_render(scene, cam, prm)
+    assert np.isfinite(img).all()
+    for win in WINDOWS_1080:
+        (e_ok, amb, e_amb), ref, d = crop_compare(scene, cam, prm, win, img)
+        print(f"K={K} window {win}: err {e_ok:.2e}, ambiguous {amb:.4f} (err {e_amb:.2e}), "
+              f"frags/px mean {d['n_frag'].mean():.1f} max {d['n_frag'].max()}")
+        assert e_ok <= IMAGE_TOL
+        assert amb <= 0.01
+
+
+def test_config2_counters_and_instances(cfg2_scene):
+    scene, cam = cfg2_scene
+    prm = scenes.Params(K=8)
+    img, r, g = gpu_render(scene, cam, prm)
+    c = B.htgs_get_counters(r.workspace)
+    print("instances", r.last_instances, c)
+    assert c["kept"] > 0 and c["box_pairs"] >= c["kept"] // 4
+    assert r.last_instances > scene.n // 4
+
+
+@pytest.mark.parametrize("K", [4, 8, 16, 32])
+def test_config5_stress(K):
+    scene, cam, _ = scenes.config5()
+    cam = cam.rounded()
+    prm = scenes.Params(K=K)
+    g = GaussianTensors.from_scene(scene)
+    r = Renderer(cam, prm, scene.n)
+    img = r.forward(g)
+    dl = torch.randn_like(img)
+    grads = r.backward(g, dl)
+    torch.cuda.synchronize()
+    assert torch.isfinite(img).all()
+    for k, v in grads.items():
+        assert torch.isfinite(v).all(), k
+    win = (952, 532, 16, 16)
+    (e_ok, amb, e_amb), ref, d = crop_compare(scene, cam, prm, win, img.cpu().numpy().astype(np.float64))
+    print(f"stress K={K}: err {e_ok:.2e}, ambiguous {amb:.4f} (err {e_amb:.2e}), "
+          f"frags/px {d['n_frag'].mean():.1f}, instances {r.last_instances}")
+    assert e_ok <= IMAGE_TOL and amb <= 0.02
