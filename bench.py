@@ -141,6 +141,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(which: str, warmup: int):
+    """A few untimed steps of the headline render (fwd) or of the training
+    step (train): `warmup` steps, then 2 more, nothing else on the GPU."""
+    import torch
+    from paper_2410_08129_gb300 import binding as B
+    from paper_2410_08129_gb300 import scenes
+    from paper_2410_08129_gb300.renderer import GaussianTensors, Renderer
+    if which == "fwd":
+        scene, cam, prm = scenes.config2()
+        g = GaussianTensors.from_scene(scene)
+        r = Renderer(cam.rounded(), prm, scene.n)
+        img = r.image_buffer()
+        r.forward(g, image=img, save=False, check=True)
+        for _ in range(warmup + 2):
+            r.forward(g, image=img, save=False, check=False)
+    else:
+        scene, target, cam, prm = scenes.config3()
+        g = GaussianTensors.from_scene(scene)
+        r = Renderer(cam.rounded(), prm, scene.n)
+        img = r.image_buffer()
+        tgt = r.forward(GaussianTensors.from_scene(target), save=False, check=True).clone()
+        dl = torch.empty_like(img)
+        loss = torch.zeros(1, device="cuda")
+        r.forward(g, image=img, save=True, check=True)
+        for _ in range(warmup + 2):
+            r.forward(g, image=img, save=True, check=False)
+            B._check(B.htgs_l1_loss_grad(img, tgt, dl, loss), "l1")
+            r.backward(g, dl)
+    torch.cuda.synchronize()
+    st, inst = r.status()
+    assert st == B.HTGS_OK, st
+    print(f"profile case {which}: ok, {inst} instances")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -148,9 +182,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["fwd", "train"], default=None,
+                    help="run a few untimed steps of one workload (for an external profiler) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile:
+        profile_case(args.profile, args.warmup)
         return
 
     import torch

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
         const int nb = (int)min((uint32_t)kBatch, range.y - b0);
         __syncthreads();
-        if (tid < nb) s_gid[tid] = a.vals[b0 + tid];
+        for (int k = tid; k < nb; k += NT) s_gid[k] = a.vals[b0 + k];
         __syncthreads();
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_bwd_kernel(BlendBwdArgs a)
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
         const int nb = (int)min((uint32_t)kBatch, range.y - b0);
         __syncthreads();
-        if (tid < nb) s_gid[tid] = a.vals[b0 + tid];
+        for (int k = tid; k < nb; k += NT) s_gid[k] = a.vals[b0 + k];
         __syncthreads();
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;

@@ -83,6 +83,8 @@ def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, names=FIELDS):
         bound = rel_elem * np.maximum(np.abs(b), 1e-3 * mx) + 1e-9
         worst = float(np.max(np.abs(a - b) / bound))
         report[f] = (rn, worst)
-        assert rn <= rel_norm, (f, rn)
-        assert worst <= 1.0, (f, worst, int(np.argmax(np.abs(a - b) / bound)))
+        k = int(np.argmax(np.abs(a - b) / bound))
+        detail = dict(field=f, rel_norm=rn, worst=worst, index=k, got=float(a[k]), want=float(b[k]), max_abs=mx)
+        assert rn <= rel_norm, detail
+        assert worst <= 1.0, detail
     return report
