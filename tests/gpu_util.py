@@ -11,6 +11,10 @@ from paper_2410_08129_gb300.renderer import FIELDS, GaussianTensors, Renderer
 
 # Per-channel tolerance of the image (FP32 path vs FP64 oracle).
 IMAGE_TOL = 2e-4
+# Largest share of pixels on which a near-decision (cutoff, tau_K, depth tie)
+# could flip between FP32 and FP64 and move the colour by more than 2e-5;
+# those pixels are excluded from the element-by-element comparison.
+MAX_AMBIGUOUS = 0.03
 
 
 def gpu_render(scene, cam, params, tile=(16, 16), ppt=0, capacity=None, save=True):
@@ -67,10 +71,13 @@ def grads_to_numpy(grads):
     return {f: grads[f].detach().cpu().numpy().astype(np.float64) for f in FIELDS}
 
 
-def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, names=FIELDS):
+def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, floor=1e-2, names=FIELDS):
     """Per tensor: ||g - ref|| <= rel_norm ||ref||, and elementwise
-    |g - ref| <= rel_elem * max(|ref|, 1e-3 * max|ref|) (+ a floor for
-    all-zero tensors)."""
+    |g - ref| <= rel_elem * max(|ref|, floor * max|ref|) (+ a floor for
+    all-zero tensors). The elementwise floor reflects FP32 accumulation: an
+    element is a sum over pixels whose terms can be as large as the tensor's
+    largest entry and cancel, so its absolute error scales with max|ref|,
+    not with its own (possibly tiny) value."""
     report = {}
     for f in names:
         a, b = g[f].reshape(-1), ref[f].reshape(-1)
@@ -80,7 +87,7 @@ def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, names=FIELDS):
             assert np.abs(a).max() <= 1e-6, (f, np.abs(a).max())
             continue
         rn = np.linalg.norm(a - b) / nb
-        bound = rel_elem * np.maximum(np.abs(b), 1e-3 * mx) + 1e-9
+        bound = rel_elem * np.maximum(np.abs(b), floor * mx) + 1e-9
         worst = float(np.max(np.abs(a - b) / bound))
         report[f] = (rn, worst)
         k = int(np.argmax(np.abs(a - b) / bound))

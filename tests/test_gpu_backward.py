@@ -80,7 +80,10 @@ def test_training_step_distribution_crop_gradients():
     x0, y0, w, h = win
     _, d = oracle.render(scene.astype(np.float64), cam, prm, window=win, diagnostics=True)
     dl_win = np.random.default_rng(3).standard_normal((h, w, 3))
-    dl_win[d["near_decision"] != 0] = 0.0
+    # Pixels about 10^4 fragments deep almost always hold some fragment near
+    # the cutoff; such a fragment has alpha ~ tau_alpha and moves gradients
+    # by far less than the tolerance, so only the other decisions are masked.
+    dl_win[(d["near_decision"] & ~oracle.AMB_CUTOFF) != 0] = 0.0
     dl = np.zeros((cam.height, cam.width, 3), np.float32)
     dl[y0:y0 + h, x0:x0 + w] = dl_win
     ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl_win, window=win)
@@ -89,4 +92,4 @@ def test_training_step_distribution_crop_gradients():
     assert touched.sum() > 1000
     rep = assert_grad_close(got, ref)
     print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()}, "touched", int(touched.sum()),
-          "masked", float((d["near_decision"] != 0).mean()), "instances", r.last_instances)
+          "masked", float(((d["near_decision"] & ~oracle.AMB_CUTOFF) != 0).mean()), "instances", r.last_instances)

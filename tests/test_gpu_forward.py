@@ -11,7 +11,8 @@ import oracle
 from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
 from paper_2410_08129_gb300.renderer import GaussianTensors, Renderer
-from tests.gpu_util import (IMAGE_TOL, compare_images, gpu_render, saved_planes, workspace_view)
+from tests.gpu_util import (IMAGE_TOL, MAX_AMBIGUOUS, compare_images, gpu_render, saved_planes,
+                            workspace_view)
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +32,7 @@ def test_config1_image_parity(cfg1):
     print(f"config1: max err {e_ok:.3e} on unambiguous pixels, ambiguous {amb_frac:.4f} (max err {e_amb:.3e})")
     assert np.isfinite(img).all()
     assert e_ok <= IMAGE_TOL
-    assert amb_frac <= 0.01
+    assert amb_frac <= MAX_AMBIGUOUS
 
 
 def test_config1_core_ids_match(cfg1):
@@ -111,7 +112,7 @@ def test_k_values(K):
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
     e_ok, amb_frac, e_amb = compare_images(img, ref, d["ambiguous"])
     print(f"K={K}: err {e_ok:.3e} amb {amb_frac:.4f} ({e_amb:.3e}), frags/px max {d['n_frag'].max()}")
-    assert e_ok <= IMAGE_TOL and amb_frac <= 0.02
+    assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS
 
 
 def test_ragged_image_and_big_splats():
@@ -124,7 +125,7 @@ def test_ragged_image_and_big_splats():
         img, r, g = gpu_render(scene, cam, prm, tile=tile)
         ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
         e_ok, amb_frac, _ = compare_images(img, ref, d["ambiguous"])
-        assert e_ok <= IMAGE_TOL and amb_frac <= 0.02, (tile, e_ok, amb_frac)
+        assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS, (tile, e_ok, amb_frac)
 
 
 def test_empty_and_culled_scenes():
