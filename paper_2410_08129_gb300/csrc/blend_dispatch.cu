@@ -7,10 +7,6 @@ bool blend_fwd_k4(const BlendFwdArgs &a, int ppt, cudaStream_t s);
 bool blend_fwd_k8(const BlendFwdArgs &a, int ppt, cudaStream_t s);
 bool blend_fwd_k16(const BlendFwdArgs &a, int ppt, cudaStream_t s);
 bool blend_fwd_k32(const BlendFwdArgs &a, int ppt, cudaStream_t s);
-bool blend_bwd_k4(const BlendBwdArgs &a, int ppt, cudaStream_t s);
-bool blend_bwd_k8(const BlendBwdArgs &a, int ppt, cudaStream_t s);
-bool blend_bwd_k16(const BlendBwdArgs &a, int ppt, cudaStream_t s);
-bool blend_bwd_k32(const BlendBwdArgs &a, int ppt, cudaStream_t s);
 
 bool launch_blend_fwd(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
     const int K = a.prm.K;
@@ -18,15 +14,6 @@ bool launch_blend_fwd(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
     if (K <= 8) return blend_fwd_k8(a, ppt, s);
     if (K <= 16) return blend_fwd_k16(a, ppt, s);
     if (K <= 32) return blend_fwd_k32(a, ppt, s);
-    return false;
-}
-
-bool launch_blend_bwd(const BlendBwdArgs &a, int ppt, cudaStream_t s) {
-    const int K = a.prm.K;
-    if (K <= 4) return blend_bwd_k4(a, ppt, s);
-    if (K <= 8) return blend_bwd_k8(a, ppt, s);
-    if (K <= 16) return blend_bwd_k16(a, ppt, s);
-    if (K <= 32) return blend_bwd_k32(a, ppt, s);
     return false;
 }
 

@@ -2,15 +2,24 @@
 // blending (arXiv 2410.08129, Sec. 3.2 Eq. (13), Sec. 3.3 Eq. (14)-(16)) and
 // its adjoint.
 //
-// One CTA per tile of TW x TH pixels; each thread owns PPT vertically
-// adjacent pixels. The tile's instance list (gid ascending, no depth order)
-// is staged through shared memory in batches of 96-byte records. For every
-// (record, pixel) pair the quadratic Q of the record decides rho^2 <= rho_c;
-// kept fragments update the per-pixel order-independent sums over all
-// fragments (sum alpha, sum alpha c, prod (1 - alpha), count) and, when
-// alpha >= tau_K, a depth-sorted K-core of 64-bit (depth, gid) keys held in
-// registers. The tail is "all fragments minus the core": its sums are
-// recovered in the epilogue, so an evicted core entry needs no colour.
+// Forward: one CTA per tile of TW x TH pixels; each warp owns an 8 x (4 PPT)
+// pixel footprint and each lane PPT vertically adjacent pixels. The tile's
+// instance list (gid ascending, no depth order) is staged through shared
+// memory in batches of records; a warp first culls a batch against its
+// footprint (one bounding-box test per lane and record, one ballot per 32
+// records) and evaluates only the records that touch it. For each pixel the
+// quadratic Q of a record decides rho^2 <= rho_c; kept fragments update the
+// per-pixel order-independent sums over all fragments (sum alpha,
+// sum alpha c, prod (1 - alpha), count) and, when alpha >= tau_K, a K-core
+// of (depth, gid) pairs held in registers in ascending order. The tail is
+// "all fragments minus the core": its sums are recovered in the epilogue,
+// so an evicted core entry needs no colour.
+//
+// Adjoint: one CTA per tile. The per-pixel adjoint state (the shared tail
+// partials of Sec. 3.3 and the core's dL/dalpha, dL/dc) is built once in
+// shared memory; then each warp takes whole records and its lanes walk the
+// pixels of the record's bounding box inside the tile, so the 16 gradient
+// accumulators of a record are reduced once per (record, tile).
 #pragma once
 
 #include "common.cuh"
@@ -19,18 +28,16 @@
 namespace htgs {
 
 constexpr int kBatch = 64;
+constexpr int kBwdThreads = 256;
 
-// Alpha and depth of one record at a pixel offset, evaluated identically in
-// the main loop, the epilogue and the adjoint.
+// Alpha of one record at a pixel offset, evaluated identically in the main
+// loop, the epilogue and the adjoint.
 struct FragEval {
     float D, rD, t, araw, alpha;
 };
 
-__device__ __forceinline__ bool frag_alpha(const float4 &c0, const float4 &c1, const float4 &c2,
-                                           const float4 &c3, float dx, float dy, float tau_alpha,
-                                           float alpha_max, float Qv, FragEval &f) {
-    (void)c0;
-    (void)c1;
+__device__ __forceinline__ bool frag_alpha(const float4 &c2, const float4 &c3, float dx, float dy,
+                                           float tau_alpha, float alpha_max, float Qv, FragEval &f) {
     f.D = quad_eval(c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, dx, dy);
     if (!(f.D > 0.f)) return false; // vanishing denominator: the ray misses
     f.rD = rcp_approx(f.D);
@@ -40,19 +47,29 @@ __device__ __forceinline__ bool frag_alpha(const float4 &c0, const float4 &c1, c
     return true;
 }
 
+__device__ __forceinline__ float frag_q(const float4 &c0, const float4 &c1, float dx, float dy) {
+    return quad_eval(c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, dx, dy);
+}
+
 __device__ __forceinline__ float frag_depth(const float4 &c3, const float4 &c4, float dx, float dy,
                                             float rD) {
     return __fmul_rn(quad_eval(c3.z, c3.w, c4.x, c4.y, c4.z, c4.w, dx, dy), rD);
 }
 
+// Insertion into an ascending (depth, gid) list. Ties in depth keep the
+// earlier entry first; records are visited in ascending gid, so the order is
+// lexicographic in (depth, gid).
 template <int KMAX>
-__device__ __forceinline__ void core_insert(unsigned long long (&core)[KMAX], unsigned long long key) {
+__device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KMAX], float z, uint32_t g) {
 #pragma unroll
     for (int i = 0; i < KMAX; ++i) {
-        const unsigned long long c = core[i];
-        const bool sw = key < c;
-        core[i] = sw ? key : c;
-        key = sw ? c : key;
+        const float oz = cz[i];
+        const uint32_t og = cg[i];
+        const bool sw = z < oz;
+        cz[i] = sw ? z : oz;
+        cg[i] = sw ? g : og;
+        z = sw ? oz : z;
+        g = sw ? og : g;
     }
 }
 
@@ -62,30 +79,43 @@ __device__ __forceinline__ void core_insert(unsigned long long (&core)[KMAX], un
 template <int KMAX, int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
+    constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
+    constexpr int WPR = TW / 8;  // footprints per tile row
+    static_assert(TW % 8 == 0 && TH % WY == 0 && NT % 32 == 0, "unsupported blend shape");
     __shared__ float4 s_rec[kBatch][kRecF4];
     __shared__ uint32_t s_gid[kBatch];
     if (a.status[kStError] != 0) return;
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles.tiles_x, ty = tile / a.tiles.tiles_x;
-    const int tid = threadIdx.x;
-    const int px_i = tx * TW + tid % TW;
-    const int py_i0 = ty * TH + (tid / TW) * PPT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wx0 = tx * TW + (warp % WPR) * 8;
+    const int wy0 = ty * TH + (warp / WPR) * WY;
+    const int px_i = wx0 + (lane & 7);
+    const int py_i0 = wy0 + (lane >> 3) * PPT;
     const float px = (float)px_i + 0.5f;
     float py[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) py[p] = (float)(py_i0 + p) + 0.5f;
+    // The warp's footprint in pixel-centre coordinates.
+    const float fx0 = (float)wx0 + 0.5f, fx1 = (float)wx0 + 7.5f;
+    const float fy0 = (float)wy0 + 0.5f, fy1 = (float)(wy0 + WY) - 0.5f;
 
     const int K = a.prm.K;
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
-    unsigned long long core[PPT][KMAX];
+    float cz[PPT][KMAX];
+    uint32_t cg[PPT][KMAX];
     float sA[PPT], sR[PPT], sG[PPT], sB[PPT], sP[PPT];
     int nall[PPT];
     uint32_t n_adm = 0, n_ins = 0;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) core[p][k] = (k < KMAX - K) ? 0ull : ~0ull;
+        for (int k = 0; k < KMAX; ++k) {
+            // Slots below KMAX - K hold -inf and are never displaced.
+            cz[p][k] = (k < KMAX - K) ? -INFINITY : INFINITY;
+            cg[p][k] = 0xffffffffu;
+        }
         sA[p] = sR[p] = sG[p] = sB[p] = 0.f;
         sP[p] = 1.f;
         nall[p] = 0;
@@ -102,40 +132,48 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
             s_rec[j][f] = a.rec[(size_t)s_gid[j] * kRecF4 + f];
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            const float4 c0 = s_rec[j][0], c1 = s_rec[j][1];
-            const float dx = __fsub_rn(px, c0.x);
-            float Q[PPT];
-            bool any = false;
-#pragma unroll
-            for (int p = 0; p < PPT; ++p) {
-                const float dy = __fsub_rn(py[p], c0.y);
-                Q[p] = quad_eval(c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, dx, dy);
-                any |= Q[p] >= 0.f;
+        for (int c = 0; c < nb; c += 32) {
+            bool hit = false;
+            if (c + lane < nb) {
+                const float4 bb = s_rec[c + lane][6];
+                hit = bb.x <= fx1 && bb.y >= fx0 && bb.z <= fy1 && bb.w >= fy0;
             }
-            if (!any) continue;
-            const float4 c2 = s_rec[j][2], c3 = s_rec[j][3], c4 = s_rec[j][4], c5 = s_rec[j][5];
-            const uint32_t gid = s_gid[j];
+            uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            while (mask) {
+                const int j = c + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 c0 = s_rec[j][0], c1 = s_rec[j][1];
+                const float dx = __fsub_rn(px, c0.x);
+                float Q[PPT];
+                bool any = false;
 #pragma unroll
-            for (int p = 0; p < PPT; ++p) {
-                if (!(Q[p] >= 0.f)) continue;
-                const float dy = __fsub_rn(py[p], c0.y);
-                FragEval f;
-                if (!frag_alpha(c0, c1, c2, c3, dx, dy, tau_alpha, alpha_max, Q[p], f)) continue;
-                const float al = f.alpha;
-                sA[p] += al;
-                sR[p] = __fmaf_rn(al, c5.x, sR[p]);
-                sG[p] = __fmaf_rn(al, c5.y, sG[p]);
-                sB[p] = __fmaf_rn(al, c5.z, sB[p]);
-                sP[p] = __fmaf_rn(-sP[p], al, sP[p]);
-                nall[p] += 1;
-                if (al >= tau_K) {
-                    const float z = frag_depth(c3, c4, dx, dy, f.rD);
-                    const unsigned long long key = make_key(z, gid);
-                    ++n_adm;
-                    if (key < core[p][KMAX - 1]) {
-                        core_insert<KMAX>(core[p], key);
-                        ++n_ins;
+                for (int p = 0; p < PPT; ++p) {
+                    Q[p] = frag_q(c0, c1, dx, __fsub_rn(py[p], c0.y));
+                    any |= Q[p] >= 0.f;
+                }
+                if (!any) continue;
+                const float4 c2 = s_rec[j][2], c3 = s_rec[j][3], c4 = s_rec[j][4], c5 = s_rec[j][5];
+                const uint32_t gid = s_gid[j];
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    if (!(Q[p] >= 0.f)) continue;
+                    const float dy = __fsub_rn(py[p], c0.y);
+                    FragEval f;
+                    if (!frag_alpha(c2, c3, dx, dy, tau_alpha, alpha_max, Q[p], f)) continue;
+                    const float al = f.alpha;
+                    sA[p] += al;
+                    sR[p] = __fmaf_rn(al, c5.x, sR[p]);
+                    sG[p] = __fmaf_rn(al, c5.y, sG[p]);
+                    sB[p] = __fmaf_rn(al, c5.z, sB[p]);
+                    sP[p] = __fmaf_rn(-sP[p], al, sP[p]);
+                    nall[p] += 1;
+                    if (al >= tau_K) {
+                        const float z = frag_depth(c3, c4, dx, dy, f.rD);
+                        ++n_adm;
+                        if (z < cz[p][KMAX - 1]) {
+                            core_insert<KMAX>(cz[p], cg[p], z, gid);
+                            ++n_ins;
+                        }
                     }
                 }
             }
@@ -154,7 +192,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
             adm += __shfl_xor_sync(0xffffffffu, adm, o);
             ins += __shfl_xor_sync(0xffffffffu, ins, o);
         }
-        if ((tid & 31) == 0 && a.stats) {
+        if (lane == 0 && a.stats) {
             atomicAdd(a.stats + kStatKept, kept);
             atomicAdd(a.stats + kStatAdmitted, adm);
             atomicAdd(a.stats + kStatInserted, ins);
@@ -174,15 +212,13 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
         int n_core = 0;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const unsigned long long key = core[p][k];
-            if (k < KMAX - K || key == ~0ull) continue;
-            const uint32_t gid = (uint32_t)(key & 0xffffffffull);
+            if (k < KMAX - K || !(cz[p][k] < INFINITY)) continue;
+            const uint32_t gid = cg[p][k];
             const float4 *r = a.rec + (size_t)gid * kRecF4;
             const float4 c0 = r[0], c1 = r[1], c2 = r[2], c3 = r[3], c5 = r[5];
             const float ex = __fsub_rn(px, c0.x), ey = __fsub_rn(py[p], c0.y);
-            const float Qv = quad_eval(c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, ex, ey);
             FragEval f;
-            frag_alpha(c0, c1, c2, c3, ex, ey, tau_alpha, alpha_max, Qv, f);
+            frag_alpha(c2, c3, ex, ey, tau_alpha, alpha_max, frag_q(c0, c1, ex, ey), f);
             const float al = f.alpha;
             const float w = al * T;
             C[0] += w * c5.x; C[1] += w * c5.y; C[2] += w * c5.z;
@@ -228,7 +264,10 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
 // has dL/dalpha_r = T_r g.(c_r - G_r) and dL/dc_r = g alpha_r T_r, with G_r
 // the colour seen behind r.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane) {
+
+// Sums 16 per-lane values over the warp; afterwards lane 8q (q = 0..3) holds
+// the sums of values 4q .. 4q + 3 in v[0..3].
+__device__ __forceinline__ void warp_reduce16_to4(float (&v)[16], int lane) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const bool up = lane & 16;
@@ -244,208 +283,197 @@ __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = lane & 4;
-        const float send = up ? v[i] : v[i + 2];
-        const float keep = up ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    {
-        const bool up = lane & 2;
-        const float send = up ? v[0] : v[1];
-        const float keep = up ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-    // Even lane l now holds the warp sum of value index l >> 1.
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
 
-template <int KMAX, int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW *TH / PPT) blend_bwd_kernel(BlendBwdArgs a) {
-    constexpr int NT = TW * TH / PPT;
-    __shared__ float4 s_rec[kBatch][kRecF4];
-    __shared__ uint32_t s_gid[kBatch];
-    __shared__ float s_acc[kBatch][16];
+// Dynamic shared memory of the adjoint for a TP-pixel tile and core size K.
+__host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
+    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float)) +
+           (size_t)kBatch * (kRecF4 * sizeof(float4) + sizeof(uint32_t));
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs a) {
+    constexpr int TP = TW * TH;
+    constexpr int NW = kBwdThreads / 32;
+    extern __shared__ float4 smem[];
+    const int K = a.prm.K;
+    float4 *s_pa = smem;                 // g.xyz, k0
+    float4 *s_pb = s_pa + TP;            // u.xyz, k1
+    float4 *s_pc = s_pb + TP;            // last core depth, last core gid, mode, -
+    float4 (*s_rec)[kRecF4] = reinterpret_cast<float4 (*)[kRecF4]>(s_pc + TP);
+    uint32_t *s_gid = reinterpret_cast<uint32_t *>(s_rec + kBatch);
+    uint32_t *s_cg = s_gid + kBatch;     // [K][TP] core gids (depth order)
+    float *s_cw = reinterpret_cast<float *>(s_cg + (size_t)K * TP); // [K][TP] dL/dalpha_r
+    float *s_cv = s_cw + (size_t)K * TP; // [K][TP] alpha_r T_r
     if (a.status[kStError] != 0) return;
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles.tiles_x, ty = tile / a.tiles.tiles_x;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int px_i = tx * TW + tid % TW;
-    const int py_i0 = ty * TH + (tid / TW) * PPT;
-    const float px = (float)px_i + 0.5f;
-    float py[PPT];
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) py[p] = (float)(py_i0 + p) + 0.5f;
-
-    const int K = a.prm.K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int x1 = min(x0 + TW, a.width) - 1, y1 = min(y0 + TH, a.height) - 1;
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
+    const float bg0 = a.prm.bg[0], bg1 = a.prm.bg[1], bg2 = a.prm.bg[2];
     const size_t npix = (size_t)a.width * a.height;
-    constexpr float kTwoLn2 = 1.3862943611198906f;
 
-    // Per-pixel constants.
-    float g[PPT][3], u[PPT][3], k0[PPT], k1[PPT];
-    uint32_t cgid[PPT][KMAX];
-    float cw[PPT][KMAX], cv[PPT][KMAX];
-    unsigned long long last_key[PPT];
-    bool core_possible[PPT];
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const int x = px_i, y = py_i0 + p;
+    // Phase A: per-pixel adjoint state.
+    for (int p = tid; p < TP; p += kBwdThreads) {
+        const int x = x0 + p % TW, y = y0 + p / TW;
         const bool inside = x < a.width && y < a.height;
         const size_t pix = inside ? (size_t)y * a.width + x : 0;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         int n_core = 0;
-        float Tc = 1.f, Pc = 1.f, At = 0.f, ct[3] = {0.f, 0.f, 0.f};
+        float Tc = 1.f, Pc = 1.f, At = 0.f, ct0 = 0.f, ct1 = 0.f, ct2 = 0.f;
         if (inside) {
-            g[p][0] = a.dl_dimg[pix * 3 + 0];
-            g[p][1] = a.dl_dimg[pix * 3 + 1];
-            g[p][2] = a.dl_dimg[pix * 3 + 2];
+            g0 = a.dl_dimg[pix * 3 + 0];
+            g1 = a.dl_dimg[pix * 3 + 1];
+            g2 = a.dl_dimg[pix * 3 + 2];
             n_core = min(max(__float_as_int(a.saved[0 * npix + pix]), 0), K);
             Tc = a.saved[1 * npix + pix];
             Pc = a.saved[2 * npix + pix];
             At = a.saved[3 * npix + pix];
-            ct[0] = a.saved[4 * npix + pix];
-            ct[1] = a.saved[5 * npix + pix];
-            ct[2] = a.saved[6 * npix + pix];
-        } else {
-            g[p][0] = g[p][1] = g[p][2] = 0.f;
+            ct0 = a.saved[4 * npix + pix];
+            ct1 = a.saved[5 * npix + pix];
+            ct2 = a.saved[6 * npix + pix];
         }
-        const float bg0 = a.prm.bg[0], bg1 = a.prm.bg[1], bg2 = a.prm.bg[2];
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f, k0 = 0.f, k1 = 0.f;
         if (At > 0.f) {
-            const float s = (Tc - Pc) / At;
-            u[p][0] = g[p][0] * s; u[p][1] = g[p][1] * s; u[p][2] = g[p][2] * s;
-            k0[p] = -(u[p][0] * ct[0] + u[p][1] * ct[1] + u[p][2] * ct[2]);
-            k1[p] = Pc * (g[p][0] * (ct[0] - bg0) + g[p][1] * (ct[1] - bg1) + g[p][2] * (ct[2] - bg2));
-        } else {
-            u[p][0] = u[p][1] = u[p][2] = 0.f;
-            k0[p] = k1[p] = 0.f;
+            const float s = __fdividef(Tc - Pc, At);
+            u0 = g0 * s; u1 = g1 * s; u2 = g2 * s;
+            k0 = -(u0 * ct0 + u1 * ct1 + u2 * ct2);
+            k1 = Pc * (g0 * (ct0 - bg0) + g1 * (ct1 - bg1) + g2 * (ct2 - bg2));
         }
-        // Colour seen behind the core: (1 - T_tail) c_tail + T_tail bg with
-        // T_tail = P / T_c.
-        const float Tt = (At > 0.f && Tc > 0.f) ? fminf(Pc / Tc, 1.f) : 1.f;
-        float G[3] = {(1.f - Tt) * ct[0] + Tt * bg0, (1.f - Tt) * ct[1] + Tt * bg1,
-                      (1.f - Tt) * ct[2] + Tt * bg2};
-        last_key[p] = ~0ull;
-        // Back to front: u_r = g.(c_r - G_r), alpha_r kept in cv.
-#pragma unroll
-        for (int r = KMAX - 1; r >= 0; --r) {
-            cgid[p][r] = 0xffffffffu;
-            cw[p][r] = 0.f;
-            cv[p][r] = 0.f;
-            const uint32_t gid = r < n_core ? __float_as_uint(a.saved[(size_t)(7 + r) * npix + pix]) : 0xffffffffu;
-            if (r < n_core && (int64_t)gid < a.n) {
+        s_pa[p] = make_float4(g0, g1, g2, k0);
+        s_pb[p] = make_float4(u0, u1, u2, k1);
+        // Colour seen behind the core: (1 - T_tail) c_tail + T_tail bg, T_tail = P / T_c.
+        const float Tt = (At > 0.f && Tc > 0.f) ? fminf(__fdividef(Pc, Tc), 1.f) : 1.f;
+        float G0 = (1.f - Tt) * ct0 + Tt * bg0, G1 = (1.f - Tt) * ct1 + Tt * bg1, G2 = (1.f - Tt) * ct2 + Tt * bg2;
+        float lastz = INFINITY;
+        uint32_t lastg = 0xffffffffu;
+        // Back to front: u_r = g.(c_r - G_r) into s_cw, alpha_r into s_cv.
+        for (int r = n_core - 1; r >= 0; --r) {
+            const uint32_t gid = __float_as_uint(a.saved[(size_t)(7 + r) * npix + pix]);
+            float ur = 0.f, al = 0.f;
+            if ((int64_t)gid < a.n) {
                 const float4 *rr = a.rec + (size_t)gid * kRecF4;
                 const float4 c0 = rr[0], c1 = rr[1], c2 = rr[2], c3 = rr[3], c5 = rr[5];
-                const float ex = __fsub_rn(px, c0.x), ey = __fsub_rn(py[p], c0.y);
-                const float Qv = quad_eval(c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, ex, ey);
+                const float ex = __fsub_rn((float)x + 0.5f, c0.x), ey = __fsub_rn((float)y + 0.5f, c0.y);
                 FragEval f;
-                frag_alpha(c0, c1, c2, c3, ex, ey, tau_alpha, alpha_max, Qv, f);
-                const float al = f.alpha;
-                cgid[p][r] = gid;
-                cw[p][r] = g[p][0] * (c5.x - G[0]) + g[p][1] * (c5.y - G[1]) + g[p][2] * (c5.z - G[2]);
-                cv[p][r] = al;
-                G[0] = al * c5.x + (1.f - al) * G[0];
-                G[1] = al * c5.y + (1.f - al) * G[1];
-                G[2] = al * c5.z + (1.f - al) * G[2];
+                frag_alpha(c2, c3, ex, ey, tau_alpha, alpha_max, frag_q(c0, c1, ex, ey), f);
+                al = f.alpha;
+                ur = g0 * (c5.x - G0) + g1 * (c5.y - G1) + g2 * (c5.z - G2);
+                G0 = al * c5.x + (1.f - al) * G0;
+                G1 = al * c5.y + (1.f - al) * G1;
+                G2 = al * c5.z + (1.f - al) * G2;
                 if (r == K - 1) {
-                    const float4 c4 = rr[4];
-                    last_key[p] = make_key(frag_depth(c3, c4, ex, ey, f.rD), gid);
+                    lastz = frag_depth(c3, rr[4], ex, ey, f.rD);
+                    lastg = gid;
                 }
             }
+            s_cg[(size_t)r * TP + p] = gid;
+            s_cw[(size_t)r * TP + p] = ur;
+            s_cv[(size_t)r * TP + p] = al;
         }
         // Front to back: T_r; dL/dalpha_r = T_r u_r, dL/dc_r = g alpha_r T_r.
         float T = 1.f;
-#pragma unroll
-        for (int r = 0; r < KMAX; ++r) {
-            const float al = cv[p][r];
-            cw[p][r] = T * cw[p][r];
-            cv[p][r] = al * T;
+        for (int r = 0; r < n_core; ++r) {
+            const float al = s_cv[(size_t)r * TP + p];
+            s_cw[(size_t)r * TP + p] *= T;
+            s_cv[(size_t)r * TP + p] = al * T;
             T = __fmaf_rn(-T, al, T);
         }
-        core_possible[p] = K > 0;
-        if (n_core < K) last_key[p] = ~0ull;
+        // mode 0: no core (K = 0); 1: every candidate is in the core; 2: compare with the last entry.
+        const int mode = K == 0 ? 0 : (n_core < K ? 1 : 2);
+        s_pc[p] = make_float4(lastz, __uint_as_float(lastg), __int_as_float(mode), 0.f);
     }
 
-    for (int k = tid; k < kBatch * 16; k += NT) (&s_acc[0][0])[k] = 0.f;
+    constexpr float kTwoLn2 = 1.3862943611198906f;
     const uint2 range = a.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
         const int nb = (int)min((uint32_t)kBatch, range.y - b0);
         __syncthreads();
-        for (int k = tid; k < nb; k += NT) s_gid[k] = a.vals[b0 + k];
+        for (int k = tid; k < nb; k += kBwdThreads) s_gid[k] = a.vals[b0 + k];
         __syncthreads();
-        for (int k = tid; k < nb * kRecF4; k += NT) {
+        for (int k = tid; k < nb * kRecF4; k += kBwdThreads) {
             const int j = k / kRecF4, f = k - j * kRecF4;
             s_rec[j][f] = a.rec[(size_t)s_gid[j] * kRecF4 + f];
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            const float4 c0 = s_rec[j][0], c1 = s_rec[j][1];
-            const float dx = __fsub_rn(px, c0.x);
-            float Q[PPT];
-            bool any = false;
-#pragma unroll
-            for (int p = 0; p < PPT; ++p) {
-                const float dy = __fsub_rn(py[p], c0.y);
-                Q[p] = quad_eval(c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, dx, dy);
-                any |= Q[p] >= 0.f;
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            const float4 c2 = s_rec[j][2], c3 = s_rec[j][3], c4 = s_rec[j][4], c5 = s_rec[j][5];
+        for (int j = warp; j < nb; j += NW) {
+            const float4 c6 = s_rec[j][6];
+            const int ix0 = (int)fmaxf(ceilf(c6.x - 0.5f), (float)x0);
+            const int ix1 = (int)fminf(floorf(c6.y - 0.5f), (float)x1);
+            const int iy0 = (int)fmaxf(ceilf(c6.z - 0.5f), (float)y0);
+            const int iy1 = (int)fminf(floorf(c6.w - 0.5f), (float)y1);
+            if (ix0 > ix1 || iy0 > iy1) continue;
+            const float4 c0 = s_rec[j][0], c1 = s_rec[j][1], c2 = s_rec[j][2], c3 = s_rec[j][3];
+            const float4 c4 = s_rec[j][4], c5 = s_rec[j][5];
             const uint32_t gid = s_gid[j];
             float v[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) v[k] = 0.f;
-#pragma unroll
-            for (int p = 0; p < PPT; ++p) {
-                if (!(Q[p] >= 0.f)) continue;
-                const float dy = __fsub_rn(py[p], c0.y);
-                FragEval f;
-                if (!frag_alpha(c0, c1, c2, c3, dx, dy, tau_alpha, alpha_max, Q[p], f)) continue;
-                const float al = f.alpha;
-                bool in_core = false;
-                if (core_possible[p] && al >= tau_K) {
-                    const unsigned long long key = make_key(frag_depth(c3, c4, dx, dy, f.rD), gid);
-                    in_core = key <= last_key[p];
-                }
-                float dA, dc0, dc1, dc2;
-                if (in_core) {
-                    float w = 0.f, s = 0.f;
-#pragma unroll
-                    for (int r = 0; r < KMAX; ++r)
-                        if (cgid[p][r] == gid) { w = cw[p][r]; s = cv[p][r]; }
-                    dA = w;
-                    dc0 = g[p][0] * s; dc1 = g[p][1] * s; dc2 = g[p][2] * s;
-                } else {
-                    const float inv = rcp_approx(1.f - al);
-                    dA = u[p][0] * c5.x + u[p][1] * c5.y + u[p][2] * c5.z + k0[p] + k1[p] * inv;
-                    dc0 = u[p][0] * al; dc1 = u[p][1] * al; dc2 = u[p][2] * al;
-                }
-                v[13] += dc0; v[14] += dc1; v[15] += dc2;
-                if (f.araw < alpha_max) {
-                    v[12] += dA * al;
-                    const float drho2 = -0.5f * al * dA;
-                    const float rho2 = c5.w - kTwoLn2 * f.t;
-                    const float dN = drho2 * f.rD;
-                    const float dD = -dN * rho2;
-                    const float mx = dx, my = dy;
-                    const float mxx = mx * mx, mxy = mx * my, myy = my * my;
-                    v[0] += dN; v[1] += dN * mx; v[2] += dN * my;
-                    v[3] += dN * mxx; v[4] += dN * mxy; v[5] += dN * myy;
-                    v[6] += dD; v[7] += dD * mx; v[8] += dD * my;
-                    v[9] += dD * mxx; v[10] += dD * mxy; v[11] += dD * myy;
+            bool touched = false;
+            for (int by = iy0; by <= iy1; by += 4) {
+                for (int bx = ix0; bx <= ix1; bx += 8) {
+                    const int x = bx + (lane & 7), y = by + (lane >> 3);
+                    if (x > ix1 || y > iy1) continue;
+                    const float dx = __fsub_rn((float)x + 0.5f, c0.x), dy = __fsub_rn((float)y + 0.5f, c0.y);
+                    const float Qv = frag_q(c0, c1, dx, dy);
+                    if (!(Qv >= 0.f)) continue;
+                    FragEval f;
+                    if (!frag_alpha(c2, c3, dx, dy, tau_alpha, alpha_max, Qv, f)) continue;
+                    const int p = (y - y0) * TW + (x - x0);
+                    const float4 PA = s_pa[p], PB = s_pb[p];
+                    const float al = f.alpha;
+                    bool in_core = false;
+                    if (al >= tau_K) {
+                        const float4 PC = s_pc[p];
+                        const int mode = __float_as_int(PC.z);
+                        if (mode == 1) {
+                            in_core = true;
+                        } else if (mode == 2) {
+                            const float z = frag_depth(c3, c4, dx, dy, f.rD);
+                            in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
+                        }
+                    }
+                    float dA, dc0, dc1, dc2;
+                    if (in_core) {
+                        float w = 0.f, s = 0.f;
+                        for (int r = 0; r < K; ++r)
+                            if (s_cg[(size_t)r * TP + p] == gid) {
+                                w = s_cw[(size_t)r * TP + p];
+                                s = s_cv[(size_t)r * TP + p];
+                                break;
+                            }
+                        dA = w;
+                        dc0 = PA.x * s; dc1 = PA.y * s; dc2 = PA.z * s;
+                    } else {
+                        const float inv = rcp_approx(1.f - al);
+                        dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + PA.w + PB.w * inv;
+                        dc0 = PB.x * al; dc1 = PB.y * al; dc2 = PB.z * al;
+                    }
+                    touched = true;
+                    v[13] += dc0; v[14] += dc1; v[15] += dc2;
+                    if (f.araw < alpha_max) {
+                        v[12] += dA * al;
+                        const float drho2 = -0.5f * al * dA;
+                        const float rho2 = c5.w - kTwoLn2 * f.t;
+                        const float dN = drho2 * f.rD;
+                        const float dD = -dN * rho2;
+                        const float mxx = dx * dx, mxy = dx * dy, myy = dy * dy;
+                        v[0] += dN; v[1] += dN * dx; v[2] += dN * dy;
+                        v[3] += dN * mxx; v[4] += dN * mxy; v[5] += dN * myy;
+                        v[6] += dD; v[7] += dD * dx; v[8] += dD * dy;
+                        v[9] += dD * mxx; v[10] += dD * mxy; v[11] += dD * myy;
+                    }
                 }
             }
-            warp_transpose_reduce16(v, lane);
-            if ((lane & 1) == 0) atomicAdd(&s_acc[j][lane >> 1], v[0]);
-        }
-        __syncthreads();
-        // Flush the batch's accumulators: one vector reduction per 4 values.
-        for (int k = tid; k < nb * 4; k += NT) {
-            const int j = k >> 2, q = k & 3;
-            const float4 s = reinterpret_cast<const float4 *>(&s_acc[j][0])[q];
-            if (s.x != 0.f || s.y != 0.f || s.z != 0.f || s.w != 0.f)
-                red_add_v4(a.acc + (size_t)s_gid[j] * 16 + q * 4, s.x, s.y, s.z, s.w);
-            reinterpret_cast<float4 *>(&s_acc[j][0])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!__any_sync(0xffffffffu, touched)) continue;
+            warp_reduce16_to4(v, lane);
+            if ((lane & 7) == 0) red_add_v4(a.acc + (size_t)gid * 16 + (lane >> 3) * 4, v[0], v[1], v[2], v[3]);
         }
     }
 }
@@ -457,25 +485,13 @@ template <int KMAX, int TW, int TH, int PPT>
 void run_fwd(const BlendFwdArgs &a, cudaStream_t s) {
     blend_fwd_kernel<KMAX, TW, TH, PPT><<<a.tiles.n_tiles, TW * TH / PPT, 0, s>>>(a);
 }
-template <int KMAX, int TW, int TH, int PPT>
-void run_bwd(const BlendBwdArgs &a, cudaStream_t s) {
-    blend_bwd_kernel<KMAX, TW, TH, PPT><<<a.tiles.n_tiles, TW * TH / PPT, 0, s>>>(a);
-}
 
 template <int KMAX, int PPT>
 bool dispatch_shape_fwd(const BlendFwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
     if (tw == 16 && th == 16) { run_fwd<KMAX, 16, 16, PPT>(a, s); return true; }
-    if (tw == 16 && th == 8) { run_fwd<KMAX, 16, 8, PPT>(a, s); return true; }
+    if (tw == 16 && th == 8 && PPT <= 2) { run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2)>(a, s); return true; }
     if (tw == 8 && th == 8 && PPT <= 2) { run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(a, s); return true; }
-    return false;
-}
-template <int KMAX, int PPT>
-bool dispatch_shape_bwd(const BlendBwdArgs &a, cudaStream_t s) {
-    const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
-    if (tw == 16 && th == 16) { run_bwd<KMAX, 16, 16, PPT>(a, s); return true; }
-    if (tw == 16 && th == 8) { run_bwd<KMAX, 16, 8, PPT>(a, s); return true; }
-    if (tw == 8 && th == 8 && PPT <= 2) { run_bwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(a, s); return true; }
     return false;
 }
 

@@ -1,4 +1,4 @@
-// blend_k16.cu -- blend kernels with a 16-entry register core (instantiation unit).
+// blend_k16.cu -- forward blend with a 16-entry register core (instantiation unit).
 #include "blend_impl.cuh"
 
 namespace htgs {
@@ -7,12 +7,6 @@ bool blend_fwd_k16(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
     if (ppt == 1) return dispatch_shape_fwd<16, 1>(a, s);
     if (ppt == 2) return dispatch_shape_fwd<16, 2>(a, s);
     return dispatch_shape_fwd<16, 1>(a, s);
-}
-
-bool blend_bwd_k16(const BlendBwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_bwd<16, 1>(a, s);
-    if (ppt == 2) return dispatch_shape_bwd<16, 2>(a, s);
-    return dispatch_shape_bwd<16, 1>(a, s);
 }
 
 } // namespace htgs

@@ -1,4 +1,4 @@
-// blend_k32.cu -- blend kernels with a 32-entry register core (instantiation unit).
+// blend_k32.cu -- forward blend with a 32-entry register core (instantiation unit).
 #include "blend_impl.cuh"
 
 namespace htgs {
@@ -6,11 +6,6 @@ namespace htgs {
 bool blend_fwd_k32(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
     if (ppt == 1) return dispatch_shape_fwd<32, 1>(a, s);
     return dispatch_shape_fwd<32, 1>(a, s);
-}
-
-bool blend_bwd_k32(const BlendBwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_bwd<32, 1>(a, s);
-    return dispatch_shape_bwd<32, 1>(a, s);
 }
 
 } // namespace htgs

@@ -1,4 +1,4 @@
-// blend_k4.cu -- blend kernels with a 4-entry register core (instantiation unit).
+// blend_k4.cu -- forward blend with a 4-entry register core (instantiation unit).
 #include "blend_impl.cuh"
 
 namespace htgs {
@@ -8,13 +8,6 @@ bool blend_fwd_k4(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
     if (ppt == 2) return dispatch_shape_fwd<4, 2>(a, s);
     if (ppt == 4) return dispatch_shape_fwd<4, 4>(a, s);
     return dispatch_shape_fwd<4, 1>(a, s);
-}
-
-bool blend_bwd_k4(const BlendBwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_bwd<4, 1>(a, s);
-    if (ppt == 2) return dispatch_shape_bwd<4, 2>(a, s);
-    if (ppt == 4) return dispatch_shape_bwd<4, 4>(a, s);
-    return dispatch_shape_bwd<4, 1>(a, s);
 }
 
 } // namespace htgs

@@ -1,4 +1,4 @@
-// blend_k8.cu -- blend kernels with a 8-entry register core (instantiation unit).
+// blend_k8.cu -- forward blend with a 8-entry register core (instantiation unit).
 #include "blend_impl.cuh"
 
 namespace htgs {
@@ -8,13 +8,6 @@ bool blend_fwd_k8(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
     if (ppt == 2) return dispatch_shape_fwd<8, 2>(a, s);
     if (ppt == 4) return dispatch_shape_fwd<8, 4>(a, s);
     return dispatch_shape_fwd<8, 1>(a, s);
-}
-
-bool blend_bwd_k8(const BlendBwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_bwd<8, 1>(a, s);
-    if (ppt == 2) return dispatch_shape_bwd<8, 2>(a, s);
-    if (ppt == 4) return dispatch_shape_bwd<8, 4>(a, s);
-    return dispatch_shape_bwd<8, 1>(a, s);
 }
 
 } // namespace htgs

@@ -42,12 +42,13 @@ struct TileArgs {
 //   [3] d4, d5, z0, z1        Z = (view depth) * D coefficients
 //   [4] z2, z3, z4, z5
 //   [5] r, g, b, rho_c        colour and cutoff
+//   [6] x0, x1, y0, y1        screen bounding box p -+ h (slightly widened)
 // Each quadratic is c0 + c1 x' + c2 y' + c3 x'^2 + c4 x'y' + c5 y'^2 in the
 // offsets (x', y') = (x - xc, y - yc) of the pixel centre. With
 // N = ||m||^2 (m the Pluecker moment), Q = log2(e) (rho_c D - N) / 2, so
 // that rho^2 = N / D <= rho_c <=> Q >= 0 and
 // alpha = o e^{-rho^2/2} = tau_alpha * 2^{Q / D}.
-constexpr int kRecF4 = 6;
+constexpr int kRecF4 = 7;
 
 // Device status word layout (int32 array at the front of the workspace).
 enum StatusSlot {

@@ -227,10 +227,12 @@ preprocess_kernel(PreArgs a) {
             // Covered pixel rectangle, widened by a small margin against rounding
             // (a wider box only adds work; the per-pixel test decides).
             const float lim[2] = {(float)(a.cam.width - 1), (float)(a.cam.height - 1)};
-            float lo[2], hi[2];
+            float lo[2], hi[2], box[4];
             bool ok = true;
             for (int ax = 0; ax < 2; ++ax) {
                 const float m = 1e-3f * hc[ax] + 1e-2f;
+                box[2 * ax] = pc[ax] - hc[ax] - m;
+                box[2 * ax + 1] = pc[ax] + hc[ax] + m;
                 lo[ax] = fmaxf(ceilf(pc[ax] - hc[ax] - 0.5f - m), 0.f);
                 hi[ax] = fminf(floorf(pc[ax] + hc[ax] - 0.5f + m), lim[ax]);
                 ok = ok && (lo[ax] <= hi[ax]);
@@ -283,6 +285,7 @@ preprocess_kernel(PreArgs a) {
                 rec[3] = make_float4(d[4], d[5], zq[0], zq[1]);
                 rec[4] = make_float4(zq[2], zq[3], zq[4], zq[5]);
                 rec[5] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), rc);
+                rec[6] = make_float4(box[0], box[1], box[2], box[3]);
             }
         }
         float4 *dst = a.rec + i * kRecF4;
