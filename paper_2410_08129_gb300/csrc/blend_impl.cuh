@@ -5,21 +5,25 @@
 // Forward: one CTA per tile of TW x TH pixels; each warp owns an 8 x (4 PPT)
 // pixel footprint and each lane PPT vertically adjacent pixels. The tile's
 // instance list (gid ascending, no depth order) is staged through shared
-// memory in batches of records; a warp first culls a batch against its
-// footprint (one bounding-box test per lane and record, one ballot per 32
-// records) and evaluates only the records that touch it. For each pixel the
-// quadratic Q of a record decides rho^2 <= rho_c; kept fragments update the
-// per-pixel order-independent sums over all fragments (sum alpha,
-// sum alpha c, prod (1 - alpha), count) and, when alpha >= tau_K, a K-core
-// of (depth, gid) pairs held in registers in ascending order. The tail is
-// "all fragments minus the core": its sums are recovered in the epilogue,
-// so an evicted core entry needs no colour.
+// memory in batches of records, double-buffered with cp.async so that the
+// gather of the next batch overlaps the evaluation of the current one. A
+// warp first culls a batch against its footprint (one bounding-box test per
+// lane and record, one ballot per 32 records) and evaluates only the records
+// that touch it. For each pixel one packed FP32x2 evaluation gives the pair
+// (Q, D) of a record: Q >= 0 decides rho^2 <= rho_c and D gives alpha. Kept
+// fragments update the per-pixel order-independent sums over all fragments
+// (sum alpha, sum alpha c, prod (1 - alpha), count) and, when
+// alpha >= tau_K, a K-core of (depth, gid) pairs held in registers in
+// ascending order. The tail is "all fragments minus the core": its sums are
+// recovered in the epilogue, so an evicted core entry needs no colour.
 //
 // Adjoint: one CTA per tile. The per-pixel adjoint state (the shared tail
 // partials of Sec. 3.3 and the core's dL/dalpha, dL/dc) is built once in
-// shared memory; then each warp takes whole records and its lanes walk the
-// pixels of the record's bounding box inside the tile, so the 16 gradient
-// accumulators of a record are reduced once per (record, tile).
+// shared memory; then every warp independently pulls whole records from a
+// shared counter (prefetching the next with cp.async into a private slot)
+// and its lanes walk the pixels of the record's bounding box inside the
+// tile, so the 16 gradient accumulators of a record are reduced once per
+// (record, tile) and no block-wide barrier is needed.
 #pragma once
 
 #include "common.cuh"
@@ -30,30 +34,26 @@ namespace htgs {
 constexpr int kBatch = 64;
 constexpr int kBwdThreads = 256;
 
-// Alpha of one record at a pixel offset, evaluated identically in the main
-// loop, the epilogue and the adjoint.
+// Alpha of one record at a pixel from its (Q, D) pair, evaluated identically
+// in the main loop, the epilogue and the adjoint.
 struct FragEval {
     float D, rD, t, araw, alpha;
 };
 
-__device__ __forceinline__ bool frag_alpha(const float4 &c2, const float4 &c3, float dx, float dy,
-                                           float tau_alpha, float alpha_max, float Qv, FragEval &f) {
-    f.D = quad_eval(c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, dx, dy);
-    if (!(f.D > 0.f)) return false; // vanishing denominator: the ray misses
+__device__ __forceinline__ bool frag_alpha(float2 qd, float tau_alpha, float alpha_max, FragEval &f) {
+    if (!(qd.x >= 0.f) || !(qd.y > 0.f)) return false; // outside the cutoff, or the ray misses
+    f.D = qd.y;
     f.rD = rcp_approx(f.D);
-    f.t = __fmul_rn(Qv, f.rD);
+    f.t = __fmul_rn(qd.x, f.rD);
     f.araw = __fmul_rn(tau_alpha, ex2_approx(f.t));
     f.alpha = fminf(f.araw, alpha_max);
     return true;
 }
 
-__device__ __forceinline__ float frag_q(const float4 &c0, const float4 &c1, float dx, float dy) {
-    return quad_eval(c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, dx, dy);
-}
-
+// View depth of the point of maximum contribution (Sec. 3.3, Eq. (14)).
 __device__ __forceinline__ float frag_depth(const float4 &c3, const float4 &c4, float dx, float dy,
                                             float rD) {
-    return __fmul_rn(quad_eval(c3.z, c3.w, c4.x, c4.y, c4.z, c4.w, dx, dy), rD);
+    return __fmul_rn(quad_eval(c3.x, c3.y, c3.z, c3.w, c4.x, c4.y, dx, dy), rD);
 }
 
 // Insertion into an ascending (depth, gid) list. Ties in depth keep the
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
     constexpr int WPR = TW / 8;  // footprints per tile row
     static_assert(TW % 8 == 0 && TH % WY == 0 && NT % 32 == 0, "unsupported blend shape");
-    __shared__ float4 s_rec[kBatch][kRecF4];
-    __shared__ uint32_t s_gid[kBatch];
+    __shared__ float4 s_rec[2][kBatch][kRecF4];
+    __shared__ uint32_t s_gid[2][kBatch];
     if (a.status[kStError] != 0) return;
 
     const int tile = blockIdx.x;
@@ -122,44 +122,65 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
     }
 
     const uint2 range = a.ranges[tile];
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
-        const int nb = (int)min((uint32_t)kBatch, range.y - b0);
-        __syncthreads();
-        for (int k = tid; k < nb; k += NT) s_gid[k] = a.vals[b0 + k];
-        __syncthreads();
+    const int nbatches = (int)((range.y - range.x + kBatch - 1) / kBatch);
+    auto batch_size = [&](int b) { return (int)min((uint32_t)kBatch, range.y - range.x - (uint32_t)b * kBatch); };
+    auto load_ids = [&](int b) {
+        const uint32_t base = range.x + (uint32_t)b * kBatch;
+        const int nb = batch_size(b);
+        for (int k = tid; k < nb; k += NT) s_gid[b & 1][k] = a.vals[base + k];
+    };
+    auto issue = [&](int b) {
+        const int nb = batch_size(b);
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
-            s_rec[j][f] = a.rec[(size_t)s_gid[j] * kRecF4 + f];
+            cp_async16(&s_rec[b & 1][j][f], a.rec + (size_t)s_gid[b & 1][j] * kRecF4 + f);
+        }
+        cp_async_commit();
+    };
+    if (nbatches > 0) {
+        load_ids(0);
+        __syncthreads();
+        issue(0);
+    }
+    for (int b = 0; b < nbatches; ++b) {
+        if (b + 1 < nbatches) {
+            load_ids(b + 1);
+            __syncthreads();
+            issue(b + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const int nb = batch_size(b);
+        const float4(*rec)[kRecF4] = s_rec[b & 1];
+        const uint32_t *gids = s_gid[b & 1];
         for (int c = 0; c < nb; c += 32) {
             bool hit = false;
             if (c + lane < nb) {
-                const float4 bb = s_rec[c + lane][6];
+                const float4 bb = rec[c + lane][6];
                 hit = bb.x <= fx1 && bb.y >= fx0 && bb.z <= fy1 && bb.w >= fy0;
             }
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {
                 const int j = c + __ffs(mask) - 1;
                 mask &= mask - 1;
-                const float4 c0 = s_rec[j][0], c1 = s_rec[j][1];
-                const float dx = __fsub_rn(px, c0.x);
-                float Q[PPT];
+                const float4 c0 = rec[j][0], c1 = rec[j][1], c2 = rec[j][2], c4 = rec[j][4];
+                const float dx = __fsub_rn(px, c4.z);
+                float2 qd[PPT];
                 bool any = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    Q[p] = frag_q(c0, c1, dx, __fsub_rn(py[p], c0.y));
-                    any |= Q[p] >= 0.f;
+                    qd[p] = quad_eval2(c0, c1, c2, dx, __fsub_rn(py[p], c4.w));
+                    any |= qd[p].x >= 0.f;
                 }
                 if (!any) continue;
-                const float4 c2 = s_rec[j][2], c3 = s_rec[j][3], c4 = s_rec[j][4], c5 = s_rec[j][5];
-                const uint32_t gid = s_gid[j];
+                const float4 c3 = rec[j][3], c5 = rec[j][5];
+                const uint32_t gid = gids[j];
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    if (!(Q[p] >= 0.f)) continue;
-                    const float dy = __fsub_rn(py[p], c0.y);
                     FragEval f;
-                    if (!frag_alpha(c2, c3, dx, dy, tau_alpha, alpha_max, Q[p], f)) continue;
+                    if (!frag_alpha(qd[p], tau_alpha, alpha_max, f)) continue;
                     const float al = f.alpha;
                     sA[p] += al;
                     sR[p] = __fmaf_rn(al, c5.x, sR[p]);
@@ -168,7 +189,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
                     sP[p] = __fmaf_rn(-sP[p], al, sP[p]);
                     nall[p] += 1;
                     if (al >= tau_K) {
-                        const float z = frag_depth(c3, c4, dx, dy, f.rD);
+                        const float z = frag_depth(c3, c4, dx, __fsub_rn(py[p], c4.w), f.rD);
                         ++n_adm;
                         if (z < cz[p][KMAX - 1]) {
                             core_insert<KMAX>(cz[p], cg[p], z, gid);
@@ -178,6 +199,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
                 }
             }
         }
+        __syncthreads();
     }
 
     // Work counters: one atomic per warp.
@@ -215,10 +237,10 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
             if (k < KMAX - K || !(cz[p][k] < INFINITY)) continue;
             const uint32_t gid = cg[p][k];
             const float4 *r = a.rec + (size_t)gid * kRecF4;
-            const float4 c0 = r[0], c1 = r[1], c2 = r[2], c3 = r[3], c5 = r[5];
-            const float ex = __fsub_rn(px, c0.x), ey = __fsub_rn(py[p], c0.y);
+            const float4 c0 = r[0], c1 = r[1], c2 = r[2], c4 = r[4], c5 = r[5];
             FragEval f;
-            frag_alpha(c2, c3, ex, ey, tau_alpha, alpha_max, frag_q(c0, c1, ex, ey), f);
+            frag_alpha(quad_eval2(c0, c1, c2, __fsub_rn(px, c4.z), __fsub_rn(py[p], c4.w)), tau_alpha,
+                       alpha_max, f);
             const float al = f.alpha;
             const float w = al * T;
             C[0] += w * c5.x; C[1] += w * c5.y; C[2] += w * c5.z;
@@ -290,8 +312,7 @@ __device__ __forceinline__ void warp_reduce16_to4(float (&v)[16], int lane) {
 
 // Dynamic shared memory of the adjoint for a TP-pixel tile and core size K.
 __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
-    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float)) +
-           (size_t)kBatch * (kRecF4 * sizeof(float4) + sizeof(uint32_t));
+    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float));
 }
 
 template <int TW, int TH>
@@ -299,15 +320,16 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
     constexpr int TP = TW * TH;
     constexpr int NW = kBwdThreads / 32;
     extern __shared__ float4 smem[];
+    __shared__ float4 s_wrec[NW][2][kRecF4];  // per-warp double-buffered record
+    __shared__ uint32_t s_wgid[NW][2];
+    __shared__ uint32_t s_next;
     const int K = a.prm.K;
     float4 *s_pa = smem;                 // g.xyz, k0
     float4 *s_pb = s_pa + TP;            // u.xyz, k1
     float4 *s_pc = s_pb + TP;            // last core depth, last core gid, mode, -
-    float4 (*s_rec)[kRecF4] = reinterpret_cast<float4 (*)[kRecF4]>(s_pc + TP);
-    uint32_t *s_gid = reinterpret_cast<uint32_t *>(s_rec + kBatch);
-    uint32_t *s_cg = s_gid + kBatch;     // [K][TP] core gids (depth order)
-    float *s_cw = reinterpret_cast<float *>(s_cg + (size_t)K * TP); // [K][TP] dL/dalpha_r
-    float *s_cv = s_cw + (size_t)K * TP; // [K][TP] alpha_r T_r
+    uint32_t *s_cg = reinterpret_cast<uint32_t *>(s_pc + TP);        // [K][TP] core gids
+    float *s_cw = reinterpret_cast<float *>(s_cg + (size_t)K * TP);  // [K][TP] dL/dalpha_r
+    float *s_cv = s_cw + (size_t)K * TP;                             // [K][TP] alpha_r T_r
     if (a.status[kStError] != 0) return;
 
     const int tile = blockIdx.x;
@@ -318,6 +340,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
     const float bg0 = a.prm.bg[0], bg1 = a.prm.bg[1], bg2 = a.prm.bg[2];
     const size_t npix = (size_t)a.width * a.height;
+    const uint2 range = a.ranges[tile];
 
     // Phase A: per-pixel adjoint state.
     for (int p = tid; p < TP; p += kBwdThreads) {
@@ -359,17 +382,17 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
             float ur = 0.f, al = 0.f;
             if ((int64_t)gid < a.n) {
                 const float4 *rr = a.rec + (size_t)gid * kRecF4;
-                const float4 c0 = rr[0], c1 = rr[1], c2 = rr[2], c3 = rr[3], c5 = rr[5];
-                const float ex = __fsub_rn((float)x + 0.5f, c0.x), ey = __fsub_rn((float)y + 0.5f, c0.y);
+                const float4 c0 = rr[0], c1 = rr[1], c2 = rr[2], c4 = rr[4], c5 = rr[5];
+                const float ex = __fsub_rn((float)x + 0.5f, c4.z), ey = __fsub_rn((float)y + 0.5f, c4.w);
                 FragEval f;
-                frag_alpha(c2, c3, ex, ey, tau_alpha, alpha_max, frag_q(c0, c1, ex, ey), f);
+                frag_alpha(quad_eval2(c0, c1, c2, ex, ey), tau_alpha, alpha_max, f);
                 al = f.alpha;
                 ur = g0 * (c5.x - G0) + g1 * (c5.y - G1) + g2 * (c5.z - G2);
                 G0 = al * c5.x + (1.f - al) * G0;
                 G1 = al * c5.y + (1.f - al) * G1;
                 G2 = al * c5.z + (1.f - al) * G2;
                 if (r == K - 1) {
-                    lastz = frag_depth(c3, rr[4], ex, ey, f.rD);
+                    lastz = frag_depth(rr[3], c4, ex, ey, f.rD);
                     lastg = gid;
                 }
             }
@@ -389,44 +412,58 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
         const int mode = K == 0 ? 0 : (n_core < K ? 1 : 2);
         s_pc[p] = make_float4(lastz, __uint_as_float(lastg), __int_as_float(mode), 0.f);
     }
+    if (tid == 0) s_next = range.x;
+    __syncthreads();
 
-    constexpr float kTwoLn2 = 1.3862943611198906f;
-    const uint2 range = a.ranges[tile];
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
-        const int nb = (int)min((uint32_t)kBatch, range.y - b0);
-        __syncthreads();
-        for (int k = tid; k < nb; k += kBwdThreads) s_gid[k] = a.vals[b0 + k];
-        __syncthreads();
-        for (int k = tid; k < nb * kRecF4; k += kBwdThreads) {
-            const int j = k / kRecF4, f = k - j * kRecF4;
-            s_rec[j][f] = a.rec[(size_t)s_gid[j] * kRecF4 + f];
+    // Phase B: warps pull records; lanes walk the record's box in the tile.
+    auto grab = [&]() -> uint32_t {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(&s_next, 1u);
+        return __shfl_sync(0xffffffffu, j, 0);
+    };
+    auto issue = [&](uint32_t j, int slot) {
+        if (lane < kRecF4) {
+            const uint32_t gid = a.vals[j];
+            cp_async16(&s_wrec[warp][slot][lane], a.rec + (size_t)gid * kRecF4 + lane);
+            if (lane == 0) s_wgid[warp][slot] = gid;
         }
-        __syncthreads();
-        for (int j = warp; j < nb; j += NW) {
-            const float4 c6 = s_rec[j][6];
-            const int ix0 = (int)fmaxf(ceilf(c6.x - 0.5f), (float)x0);
-            const int ix1 = (int)fminf(floorf(c6.y - 0.5f), (float)x1);
-            const int iy0 = (int)fmaxf(ceilf(c6.z - 0.5f), (float)y0);
-            const int iy1 = (int)fminf(floorf(c6.w - 0.5f), (float)y1);
-            if (ix0 > ix1 || iy0 > iy1) continue;
-            const float4 c0 = s_rec[j][0], c1 = s_rec[j][1], c2 = s_rec[j][2], c3 = s_rec[j][3];
-            const float4 c4 = s_rec[j][4], c5 = s_rec[j][5];
-            const uint32_t gid = s_gid[j];
-            float v[16];
+        cp_async_commit();
+    };
+    constexpr float kTwoLn2 = 1.3862943611198906f;
+    uint32_t j = grab();
+    int slot = 0;
+    if (j < range.y) issue(j, 0);
+    while (j < range.y) {
+        const uint32_t jn = grab();
+        if (jn < range.y) {
+            issue(jn, slot ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const float4 *rec = s_wrec[warp][slot];
+        const uint32_t gid = s_wgid[warp][slot];
+        const float4 c6 = rec[6];
+        const int ix0 = (int)fmaxf(ceilf(c6.x - 0.5f), (float)x0);
+        const int ix1 = (int)fminf(floorf(c6.y - 0.5f), (float)x1);
+        const int iy0 = (int)fmaxf(ceilf(c6.z - 0.5f), (float)y0);
+        const int iy1 = (int)fminf(floorf(c6.w - 0.5f), (float)y1);
+        if (ix0 <= ix1 && iy0 <= iy1) {
+            const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c3 = rec[3], c4 = rec[4], c5 = rec[5];
+            float2 acc[6];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = 0.f;
+            for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
+            float gaa = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
             bool touched = false;
             for (int by = iy0; by <= iy1; by += 4) {
                 for (int bx = ix0; bx <= ix1; bx += 8) {
                     const int x = bx + (lane & 7), y = by + (lane >> 3);
                     if (x > ix1 || y > iy1) continue;
-                    const float dx = __fsub_rn((float)x + 0.5f, c0.x), dy = __fsub_rn((float)y + 0.5f, c0.y);
-                    const float Qv = frag_q(c0, c1, dx, dy);
-                    if (!(Qv >= 0.f)) continue;
+                    const float dx = __fsub_rn((float)x + 0.5f, c4.z), dy = __fsub_rn((float)y + 0.5f, c4.w);
                     FragEval f;
-                    if (!frag_alpha(c2, c3, dx, dy, tau_alpha, alpha_max, Qv, f)) continue;
+                    if (!frag_alpha(quad_eval2(c0, c1, c2, dx, dy), tau_alpha, alpha_max, f)) continue;
                     const int p = (y - y0) * TW + (x - x0);
-                    const float4 PA = s_pa[p], PB = s_pb[p];
                     const float al = f.alpha;
                     bool in_core = false;
                     if (al >= tau_K) {
@@ -441,6 +478,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
                     }
                     float dA, dc0, dc1, dc2;
                     if (in_core) {
+                        const float4 PA = s_pa[p];
                         float w = 0.f, s = 0.f;
                         for (int r = 0; r < K; ++r)
                             if (s_cg[(size_t)r * TP + p] == gid) {
@@ -451,30 +489,42 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
                         dA = w;
                         dc0 = PA.x * s; dc1 = PA.y * s; dc2 = PA.z * s;
                     } else {
+                        const float4 PB = s_pb[p];
+                        const float k0 = s_pa[p].w;
                         const float inv = rcp_approx(1.f - al);
-                        dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + PA.w + PB.w * inv;
+                        dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + k0 + PB.w * inv;
                         dc0 = PB.x * al; dc1 = PB.y * al; dc2 = PB.z * al;
                     }
                     touched = true;
-                    v[13] += dc0; v[14] += dc1; v[15] += dc2;
+                    gc0 += dc0; gc1 += dc1; gc2 += dc2;
                     if (f.araw < alpha_max) {
-                        v[12] += dA * al;
+                        gaa += dA * al;
+                        // rho^2 = N / D: dL/dN = dL/drho^2 / D, dL/dD = -dL/dN rho^2.
                         const float drho2 = -0.5f * al * dA;
                         const float rho2 = c5.w - kTwoLn2 * f.t;
                         const float dN = drho2 * f.rD;
-                        const float dD = -dN * rho2;
-                        const float mxx = dx * dx, mxy = dx * dy, myy = dy * dy;
-                        v[0] += dN; v[1] += dN * dx; v[2] += dN * dy;
-                        v[3] += dN * mxx; v[4] += dN * mxy; v[5] += dN * myy;
-                        v[6] += dD; v[7] += dD * dx; v[8] += dD * dy;
-                        v[9] += dD * mxx; v[10] += dD * mxy; v[11] += dD * myy;
+                        const float2 nd = make_float2(dN, -dN * rho2);
+                        const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
+                        acc[0].x += nd.x; acc[0].y += nd.y;
+                        acc[1] = ffma2(nd, X, acc[1]);
+                        acc[2] = ffma2(nd, Y, acc[2]);
+                        acc[3] = ffma2(nd, fmul2(X, X), acc[3]);
+                        acc[4] = ffma2(nd, fmul2(X, Y), acc[4]);
+                        acc[5] = ffma2(nd, fmul2(Y, Y), acc[5]);
                     }
                 }
             }
-            if (!__any_sync(0xffffffffu, touched)) continue;
-            warp_reduce16_to4(v, lane);
-            if ((lane & 7) == 0) red_add_v4(a.acc + (size_t)gid * 16 + (lane >> 3) * 4, v[0], v[1], v[2], v[3]);
+            if (__any_sync(0xffffffffu, touched)) {
+                float v[16] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y,
+                               acc[4].x, acc[4].y, acc[5].x, acc[5].y, gaa, gc0, gc1, gc2};
+                warp_reduce16_to4(v, lane);
+                if ((lane & 7) == 0)
+                    red_add_v4(a.acc + (size_t)gid * 16 + (lane >> 3) * 4, v[0], v[1], v[2], v[3]);
+            }
         }
+        __syncwarp();
+        slot ^= 1;
+        j = jn;
     }
 }
 

@@ -279,11 +279,11 @@ preprocess_kernel(PreArgs a) {
                     rgb[1] += Y[k] * sh[3 * k + 1];
                     rgb[2] += Y[k] * sh[3 * k + 2];
                 }
-                rec[0] = make_float4(xc, yc, q[0], q[1]);
-                rec[1] = make_float4(q[2], q[3], q[4], q[5]);
-                rec[2] = make_float4(d[0], d[1], d[2], d[3]);
-                rec[3] = make_float4(d[4], d[5], zq[0], zq[1]);
-                rec[4] = make_float4(zq[2], zq[3], zq[4], zq[5]);
+                rec[0] = make_float4(q[0], d[0], q[1], d[1]);
+                rec[1] = make_float4(q[2], d[2], q[3], d[3]);
+                rec[2] = make_float4(q[4], d[4], q[5], d[5]);
+                rec[3] = make_float4(zq[0], zq[1], zq[2], zq[3]);
+                rec[4] = make_float4(zq[4], zq[5], xc, yc);
                 rec[5] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), rc);
                 rec[6] = make_float4(box[0], box[1], box[2], box[3]);
             }
@@ -346,14 +346,15 @@ preprocess_backward_kernel(PreBwdArgs a) {
     }
     const float4 *acc4 = reinterpret_cast<const float4 *>(a.acc + 16 * i);
     const float4 A0 = acc4[0], A1 = acc4[1], A2 = acc4[2], A3 = acc4[3];
-    const float gN[6] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y};
-    const float gD[6] = {A1.z, A1.w, A2.x, A2.y, A2.z, A2.w};
+    // Interleaved pairs (dL/dN_k, dL/dD_k), k = 0..5, then the opacity and colour sums.
+    const float gN[6] = {A0.x, A0.z, A1.x, A1.z, A2.x, A2.z};
+    const float gD[6] = {A0.y, A0.w, A1.y, A1.w, A2.y, A2.w};
     const float g_aa = A3.x;
     const float gc[3] = {A3.y, A3.z, A3.w};
 
-    const float4 r0 = a.rec[i * kRecF4];
+    const float4 r0 = a.rec[i * kRecF4 + 4]; // (z4, z5, xc, yc)
     Expansion E;
-    make_expansion(S, a.cam, r0.x, r0.y, E);
+    make_expansion(S, a.cam, r0.z, r0.w, E);
     // N = n0 + n1 x' + ..., n0 = M0.M0, n1 = 2 M0.Mx, n2 = 2 M0.My, n3 = Mx.Mx,
     // n4 = 2 Mx.My, n5 = My.My; the same for D with the d vectors.
     const V3 dM0 = 2.f * (gN[0] * E.M0 + gN[1] * E.Mx + gN[2] * E.My);
@@ -375,7 +376,7 @@ preprocess_backward_kernel(PreBwdArgs a) {
     db = db + cross(E.r, dDx); dr = dr + cross(dDx, E.b);
     dr = dr + cross(E.a, dDy); da = da + cross(dDy, E.r);
     // a = fx (MT)_1 + (cx - xc)(MT)_3, b = fy (MT)_2 + (cy - yc)(MT)_3, r = (MT)_3.
-    const float ox = a.cam.cx - r0.x, oy = a.cam.cy - r0.y;
+    const float ox = a.cam.cx - r0.z, oy = a.cam.cy - r0.w;
     V3 dA[3];
     float dmuv[3];
     dA[0] = a.cam.fx * da;           dmuv[0] = a.cam.fx * daw;
