@@ -225,7 +225,7 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     for e in ev:
         e.record(stream)
-    launch = B.c_launch((16, 16), 2, 0, ev)
+    launch = B.c_launch((16, 16), 1, 0, ev)
     r = Renderer(cam, prm, scene.n, launch=launch)
     image = r.image_buffer()
     r.forward(g, image=image, save=False, check=True)       # sizes the instance capacity
@@ -356,7 +356,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": cam.width, "height": cam.height,
-                   "K": K, "tile": "16x16", "px_per_thread": 2, "parallelism": f"replicas{world}",
+                   "K": K, "tile": "16x16", "px_per_thread": 1, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (236 MB of Gaussian parameters per frame)"},
         "phases_ms": {"preprocess": float(np.mean(pre_ms)), "binning_sort": float(np.mean(bin_ms)),
                       "blend": float(np.mean(blend_ms))},

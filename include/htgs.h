@@ -99,7 +99,7 @@ typedef struct {
  *           the blend adjoint and [2]/[3] around the preprocess adjoint. */
 typedef struct {
     int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 16x8 or 8x8 */
-    int32_t px_per_thread;    /* pixels per thread in the blend: 1, 2 (default) or 4 */
+    int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4 */
     int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */
     void *events[6];
 } htgs_launch;
@@ -116,7 +116,7 @@ htgs_status htgs_workspace_size(int64_t n_gaussians, const htgs_camera *cam,
 
 /* Byte offsets of the internal buffers inside a workspace, for inspection by
  * tests and tools; their contents are valid after htgs_render has run.
- *   rec          n x 6 float4: per-Gaussian blend record
+ *   rec          n x 8 float4: per-Gaussian blend record (128 bytes)
  *   rect         n x uint2: covered tiles (tx0 | tx1 << 16, ty0 | ty1 << 16)
  *   count        n x uint32: covered tile count
  *   sorted_keys  capacity x uint32: tile keys after the radix sort

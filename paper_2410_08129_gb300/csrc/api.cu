@@ -250,7 +250,7 @@ htgs_status htgs_render(const htgs_gaussians *g, const htgs_camera *cam, const h
     ba.width = cam->width; ba.height = cam->height;
     ba.image = image; ba.saved = saved;
     ba.stats = at<unsigned long long>(workspace, L.stats);
-    const int ppt = (launch && launch->px_per_thread) ? launch->px_per_thread : 2;
+    const int ppt = (launch && launch->px_per_thread) ? launch->px_per_thread : 1;
     mark(launch, 3, s);
     mark(launch, 4, s);
     if (!launch_blend_fwd(ba, ppt, s)) return HTGS_ERR_NOT_SUPPORTED;

@@ -77,7 +77,8 @@ __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KM
 // Forward (K6).
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a) {
+__global__ void __launch_bounds__(TW *TH / PPT, (PPT >= 2 && KMAX * PPT <= 16) ? 768 / (TW * TH / PPT) : 1)
+blend_fwd_kernel(BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
     constexpr int WPR = TW / 8;  // footprints per tile row
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
                 }
                 if (!any) continue;
                 const float4 c3 = rec[j][3], c5 = rec[j][5];
+                const float zlo = rec[j][7].x;
                 const uint32_t gid = gids[j];
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
@@ -189,11 +191,15 @@ __global__ void __launch_bounds__(TW *TH / PPT) blend_fwd_kernel(BlendFwdArgs a)
                     sP[p] = __fmaf_rn(-sP[p], al, sP[p]);
                     nall[p] += 1;
                     if (al >= tau_K) {
-                        const float z = frag_depth(c3, c4, dx, __fsub_rn(py[p], c4.w), f.rD);
                         ++n_adm;
-                        if (z < cz[p][KMAX - 1]) {
-                            core_insert<KMAX>(cz[p], cg[p], z, gid);
-                            ++n_ins;
+                        // Every depth of this splat is >= zlo: skip the depth
+                        // when it cannot beat the current K-th entry.
+                        if (zlo < cz[p][KMAX - 1]) {
+                            const float z = frag_depth(c3, c4, dx, __fsub_rn(py[p], c4.w), f.rD);
+                            if (z < cz[p][KMAX - 1]) {
+                                core_insert<KMAX>(cz[p], cg[p], z, gid);
+                                ++n_ins;
+                            }
                         }
                     }
                 }
@@ -316,7 +322,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(BlendBwdArgs a) {
     constexpr int TP = TW * TH;
     constexpr int NW = kBwdThreads / 32;
     extern __shared__ float4 smem[];
@@ -451,19 +457,24 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
         const int iy1 = (int)fminf(floorf(c6.w - 0.5f), (float)y1);
         if (ix0 <= ix1 && iy0 <= iy1) {
             const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c3 = rec[3], c4 = rec[4], c5 = rec[5];
+            const float zlo = rec[7].x;
             float2 acc[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
             float gaa = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
             bool touched = false;
+            const int lx = lane & 7, ly = lane >> 3;
             for (int by = iy0; by <= iy1; by += 4) {
+                const int y = by + ly;
+                const float dy = __fsub_rn((float)y + 0.5f, c4.w);
+                const int prow = (y - y0) * TW - x0;
                 for (int bx = ix0; bx <= ix1; bx += 8) {
-                    const int x = bx + (lane & 7), y = by + (lane >> 3);
+                    const int x = bx + lx;
                     if (x > ix1 || y > iy1) continue;
-                    const float dx = __fsub_rn((float)x + 0.5f, c4.z), dy = __fsub_rn((float)y + 0.5f, c4.w);
+                    const float dx = __fsub_rn((float)x + 0.5f, c4.z);
                     FragEval f;
                     if (!frag_alpha(quad_eval2(c0, c1, c2, dx, dy), tau_alpha, alpha_max, f)) continue;
-                    const int p = (y - y0) * TW + (x - x0);
+                    const int p = prow + x;
                     const float al = f.alpha;
                     bool in_core = false;
                     if (al >= tau_K) {
@@ -471,7 +482,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) blend_bwd_kernel(BlendBwdArgs 
                         const int mode = __float_as_int(PC.z);
                         if (mode == 1) {
                             in_core = true;
-                        } else if (mode == 2) {
+                        } else if (mode == 2 && !(zlo > PC.x)) {
+                            // (depths of this splat are >= zlo, so zlo > last
+                            // core depth means the fragment is not in the core)
                             const float z = frag_depth(c3, c4, dx, dy, f.rD);
                             in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
                         }

@@ -35,7 +35,7 @@ struct TileArgs {
     int depth_bits;  // low key bits holding quantised depth
 };
 
-// Per-Gaussian blend record: 28 floats = 112 bytes = 7 float4.
+// Per-Gaussian blend record: 32 floats = 128 bytes = 8 float4.
 //   [0] q0, d0, q1, d1        Q and D coefficients, interleaved in pairs
 //   [1] q2, d2, q3, d3
 //   [2] q4, d4, q5, d5
@@ -43,13 +43,16 @@ struct TileArgs {
 //   [4] z4, z5, xc, yc        ... and the expansion centre (box centre)
 //   [5] r, g, b, rho_c        colour and cutoff
 //   [6] x0, x1, y0, y1        screen bounding box p -+ h (slightly widened)
+//   [7] zlo, -, -, -          lower bound on the view depth of every kept
+//                             fragment: the cutoff ellipsoid's nearest z,
+//                             lowered by a margin that covers rounding
 // Each quadratic is c0 + c1 x' + c2 y' + c3 x'^2 + c4 x'y' + c5 y'^2 in the
 // offsets (x', y') = (x - xc, y - yc) of the pixel centre. With
 // N = ||m||^2 (m the Pluecker moment) and D = ||d||^2 (d the direction),
 // Q = log2(e) (rho_c D - N) / 2, so that rho^2 = N / D <= rho_c <=> Q >= 0
 // and alpha = o e^{-rho^2/2} = tau_alpha * 2^{Q / D}. The (Q, D) pairs let
 // one packed FP32x2 evaluation produce both.
-constexpr int kRecF4 = 7;
+constexpr int kRecF4 = 8;
 
 // Device status word layout (int32 array at the front of the workspace).
 enum StatusSlot {
@@ -123,13 +126,6 @@ __device__ __forceinline__ float quad_eval(float c0, float c1, float c2, float c
     float tx = __fmaf_rn(c4, y, __fmaf_rn(c3, x, c1));
     float ty = __fmaf_rn(c5, y, c2);
     return __fmaf_rn(y, ty, __fmaf_rn(x, tx, c0));
-}
-
-__device__ __forceinline__ unsigned long long make_key(float z, uint32_t gid) {
-    // z > 0 for every kept fragment (the near cull keeps whole cutoff
-    // ellipsoids in front of the camera); non-negative floats order like
-    // their bit patterns. Ties break by gid.
-    return ((unsigned long long)__float_as_uint(fmaxf(z, 0.0f)) << 32) | gid;
 }
 
 // 16-byte asynchronous global -> shared copy (L2 only); completion is

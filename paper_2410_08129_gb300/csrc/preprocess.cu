@@ -286,6 +286,11 @@ preprocess_kernel(PreArgs a) {
                 rec[4] = make_float4(zq[4], zq[5], xc, yc);
                 rec[5] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), rc);
                 rec[6] = make_float4(box[0], box[1], box[2], box[3]);
+                // The point of maximum contribution lies inside the cutoff
+                // ellipsoid, whose view depth spans mu_z -+ sqrt(rho_c |A_3|^2).
+                const float zext = sqrtf(rc * dot(S.A[2], S.A[2]));
+                const float zlo = (S.mu[2] - zext) - 1e-3f * zext - 1e-4f * fabsf(S.mu[2]);
+                rec[7] = make_float4(zlo, 0.f, 0.f, 0.f);
             }
         }
         float4 *dst = a.rec + i * kRecF4;
