@@ -77,7 +77,7 @@ __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KM
 // Forward (K6).
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW *TH / PPT, (PPT >= 2 && KMAX * PPT <= 16) ? 768 / (TW * TH / PPT) : 1)
+__global__ void __launch_bounds__(TW *TH / PPT, (PPT == 1 && KMAX <= 8) ? 1024 / (TW * TH / PPT) : 1)
 blend_fwd_kernel(BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
