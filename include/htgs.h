@@ -186,6 +186,29 @@ htgs_status htgs_get_counters(void *workspace, size_t workspace_bytes, void *str
 htgs_status htgs_l1_loss_grad(const float *image, const float *target, int64_t n, float *dl_dimage,
                               float *loss, void *stream);
 
+/* Size of the scratch array that htgs_render_static keeps on every device. */
+#define HTGS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* Forward render that allocates nothing: the same result as htgs_render
+ * (no saved state), with all scratch memory in a fixed 32 MiB array that the
+ * library defines on every device that loads it. For callers that must not
+ * allocate device memory themselves, e.g. a plugin inside a host
+ * application that owns the device heap, or a real-time loop where an
+ * allocation (which may synchronise the device) is not allowed. The paper
+ * has no counterpart of this entry point.
+ *   image   [out] height x width x 3 float32, device (caller-owned)
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture. The call synchronises `stream` before returning and returns
+ * HTGS_ERR_WORKSPACE when the scene needs more scratch than the array holds
+ * (too many Gaussians for 32 MiB) and HTGS_ERR_OVERFLOW when its tile
+ * instances do not fit the rest of it. Every call shares the one array and
+ * the render clears what must start at zero; calls that overlap on the GPU
+ * (two streams, or two host threads on one device) race on it. */
+htgs_status htgs_render_static(const htgs_gaussians *gaussians, const htgs_camera *cam,
+                               const htgs_params *params, const htgs_launch *launch, float *image,
+                               void *stream);
+
 /* Static string for a status code. */
 const char *htgs_status_string(htgs_status status);
 

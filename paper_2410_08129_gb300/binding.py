@@ -96,6 +96,9 @@ def lib():
             L.htgs_l1_loss_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.htgs_l1_loss_grad.restype = ctypes.c_int32
+            L.htgs_render_static.argtypes = [P(Gaussians), P(Camera), P(Params), P(Launch), ctypes.c_void_p,
+                                             ctypes.c_void_p]
+            L.htgs_render_static.restype = ctypes.c_int32
             L.htgs_status_string.argtypes = [ctypes.c_int32]
             L.htgs_status_string.restype = ctypes.c_char_p
             for f in ("htgs_workspace_size", "htgs_render", "htgs_render_backward", "htgs_get_error",
@@ -225,4 +228,15 @@ def htgs_get_counters(workspace, stream=None):
 def htgs_l1_loss_grad(image, target, dl_dimage, loss, stream=None):
     st = lib().htgs_l1_loss_grad(_ptr(image), _ptr(target), int(image.numel()), _ptr(dl_dimage), _ptr(loss),
                                  _stream(stream))
+    return int(st)
+
+
+def htgs_render_static(gaussians: Gaussians, cam, params, launch, image, stream=None):
+    """Forward render whose scratch lives in the library's own fixed-size
+    device array: for callers that cannot allocate device memory. Returns the
+    status (synchronises the stream)."""
+    st = lib().htgs_render_static(ctypes.byref(gaussians), ctypes.byref(c_camera(cam)),
+                                  ctypes.byref(c_params(params)),
+                                  ctypes.byref(launch) if launch is not None else None, _ptr(image),
+                                  _stream(stream))
     return int(st)
