@@ -160,6 +160,55 @@ htgs_status htgs_render_backward(const htgs_gaussians *gaussians, const htgs_cam
                                  const float *saved, const float *dl_dimage,
                                  const htgs_gaussians_grad *grads, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many views (of uneven resolution, of one scene or of several
+ * scenes of uneven size) rendered by one launch per phase. The blend is a
+ * persistent kernel over a (view, tile) work queue; nothing synchronises
+ * the stream, so a batch can be captured in a CUDA graph. Results are those
+ * of rendering each view alone. The paper renders one view at a time (Sec.
+ * 4); batching is this library's addition.
+ * ------------------------------------------------------------------------- */
+#define HTGS_MAX_VIEWS 64
+
+/* One view of a batch. All pointers are device pointers except `gaussians`
+ * and `grads`, which point to host structs holding device pointers.
+ *   gaussians  the scene this view renders; several views may share one
+ *   camera     the view's camera (its own resolution)
+ *   image      [out] height x width x 3 (htgs_render_batch)
+ *   saved      [out/in] (7 + K) * width * height floats; written by
+ *              htgs_render_batch when non-NULL, read by the backward
+ *   dl_dimage  height x width x 3 (htgs_render_batch_backward only)
+ *   grads      [out] (backward only). Views that share a scene must pass
+ *              the same grads; their gradients are summed (the buffers are
+ *              zeroed by the call). A view with its own grads gets them
+ *              overwritten. */
+typedef struct {
+    const htgs_gaussians *gaussians;
+    htgs_camera camera;
+    float *image;
+    float *saved;
+    const float *dl_dimage;
+    const htgs_gaussians_grad *grads;
+} htgs_view;
+
+/* Workspace bytes for a batch of n_views (1..HTGS_MAX_VIEWS) views sharing
+ * one instance_capacity (tile instances over all views). Host pointers. */
+htgs_status htgs_batch_workspace_size(int32_t n_views, const htgs_view *views,
+                                      const htgs_params *params, const htgs_launch *launch,
+                                      int64_t instance_capacity, size_t *workspace_bytes);
+
+/* Forward render of every view of a batch (Eq. (15) per pixel of each view).
+ * Errors and overflow as for htgs_render (htgs_get_error on the workspace). */
+htgs_status htgs_render_batch(int32_t n_views, const htgs_view *views, const htgs_params *params,
+                              const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                              int64_t instance_capacity, void *stream);
+
+/* Backward of htgs_render_batch (same views, workspace and inputs). */
+htgs_status htgs_render_batch_backward(int32_t n_views, const htgs_view *views,
+                                       const htgs_params *params, const htgs_launch *launch,
+                                       void *workspace, size_t workspace_bytes,
+                                       int64_t instance_capacity, void *stream);
+
 /* Reads the device status word of a workspace after synchronising `stream`.
  *   status              [out] HTGS_OK, HTGS_ERR_OVERFLOW or HTGS_ERR_TIMEOUT
  *   instances           [out] nullable; tile instances of the last render

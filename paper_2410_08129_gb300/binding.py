@@ -240,3 +240,73 @@ def htgs_render_static(gaussians: Gaussians, cam, params, launch, image, stream=
                                   ctypes.byref(launch) if launch is not None else None, _ptr(image),
                                   _stream(stream))
     return int(st)
+
+
+# -- batched form --------------------------------------------------------------
+
+HTGS_MAX_VIEWS = 64
+
+
+class View(ctypes.Structure):
+    _fields_ = [("gaussians", ctypes.POINTER(Gaussians)), ("camera", Camera), ("image", ctypes.c_void_p),
+                ("saved", ctypes.c_void_p), ("dl_dimage", ctypes.c_void_p),
+                ("grads", ctypes.POINTER(GaussiansGrad))]
+
+
+def c_views(gaussians_structs, cams, images, saved=None, dl_dimages=None, grads=None):
+    """Array of htgs_view; the referenced structs are kept alive on the array."""
+    n = len(cams)
+    arr = (View * n)()
+    keep = []
+    for i in range(n):
+        g = gaussians_structs[i]
+        keep.append(g)
+        arr[i].gaussians = ctypes.pointer(g)
+        arr[i].camera = c_camera(cams[i])
+        arr[i].image = _ptr(images[i]) if images is not None and images[i] is not None else None
+        arr[i].saved = _ptr(saved[i]) if saved is not None and saved[i] is not None else None
+        arr[i].dl_dimage = _ptr(dl_dimages[i]) if dl_dimages is not None else None
+        if grads is not None:
+            keep.append(grads[i])
+            arr[i].grads = ctypes.pointer(grads[i])
+    arr._keep = keep
+    return arr
+
+
+def _batch_lib():
+    L = lib()
+    if not hasattr(L, "_batch_ready"):
+        P = ctypes.POINTER
+        L.htgs_batch_workspace_size.argtypes = [ctypes.c_int32, P(View), P(Params), P(Launch), ctypes.c_int64,
+                                                P(ctypes.c_size_t)]
+        L.htgs_batch_workspace_size.restype = ctypes.c_int32
+        for f in ("htgs_render_batch", "htgs_render_batch_backward"):
+            getattr(L, f).argtypes = [ctypes.c_int32, P(View), P(Params), P(Launch), ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.c_int64, ctypes.c_void_p]
+            getattr(L, f).restype = ctypes.c_int32
+        L._batch_ready = True
+    return L
+
+
+def htgs_batch_workspace_size(views, params, launch, capacity):
+    out = ctypes.c_size_t()
+    st = _batch_lib().htgs_batch_workspace_size(len(views), views, ctypes.byref(c_params(params)),
+                                                ctypes.byref(launch) if launch is not None else None,
+                                                int(capacity), ctypes.byref(out))
+    _check(st, "htgs_batch_workspace_size")
+    return int(out.value)
+
+
+def htgs_render_batch(views, params, launch, workspace, capacity, stream=None):
+    return int(_batch_lib().htgs_render_batch(len(views), views, ctypes.byref(c_params(params)),
+                                              ctypes.byref(launch) if launch is not None else None,
+                                              _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                              int(capacity), _stream(stream)))
+
+
+def htgs_render_batch_backward(views, params, launch, workspace, capacity, stream=None):
+    return int(_batch_lib().htgs_render_batch_backward(len(views), views, ctypes.byref(c_params(params)),
+                                                       ctypes.byref(launch) if launch is not None else None,
+                                                       _ptr(workspace),
+                                                       workspace.numel() * workspace.element_size(),
+                                                       int(capacity), _stream(stream)))

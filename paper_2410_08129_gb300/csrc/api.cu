@@ -1,6 +1,12 @@
 // api.cu -- the C ABI declared in include/htgs.h: argument checks, the
 // workspace layout and the launch sequence of the render path
 // (arXiv 2410.08129, Sec. 3.2-3.3; tiling as in Sec. 4.3).
+//
+// Every render is a batch of views; the single-view entry points build a
+// batch of one. The launch sequence per batch is fixed: memset of the zeroed
+// workspace region, preprocess, scan, emit, histogram + onesweep passes,
+// ranges, persistent blend. Nothing synchronises the stream, so the whole
+// sequence can be captured in a CUDA graph.
 #include <cmath>
 #include <cstring>
 
@@ -13,73 +19,97 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int64_t kMaxCapacity = (1ll << 30) - 1; // look-back count field
-constexpr int64_t kMaxGaussians = 0xfffffffell;   // gids are 32-bit
+constexpr int64_t kMaxRecords = 0xfffffffell;     // record ids are 32-bit
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     // byte offsets inside the workspace
-    size_t status, stats, total, ghist, tickets, ranges, lookback, zero_end;
-    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, acc, end;
+    size_t status, stats, total, work, ghist, tickets, ranges, lookback, zero_end;
+    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, bwd_work, acc, end;
     int n_blocks, n_sort_blocks, passes;
     TileArgs tiles;
-    size_t saved_floats;
+    int64_t n_rec;
 };
 
-bool make_tiles(const htgs_camera *cam, const htgs_launch *launch, TileArgs &t) {
+bool tile_shape(const htgs_launch *launch, TileArgs &t) {
     t.tile_w = (launch && launch->tile_w) ? launch->tile_w : 16;
     t.tile_h = (launch && launch->tile_h) ? launch->tile_h : 16;
     t.depth_bits = launch ? launch->depth_bits : 0;
     const bool shape_ok = (t.tile_w == 16 && t.tile_h == 16) || (t.tile_w == 16 && t.tile_h == 8) ||
                           (t.tile_w == 8 && t.tile_h == 8);
-    if (!shape_ok || t.depth_bits != 0) return false;
-    t.tiles_x = (cam->width + t.tile_w - 1) / t.tile_w;
-    t.tiles_y = (cam->height + t.tile_h - 1) / t.tile_h;
-    if (t.tiles_x > 65535 || t.tiles_y > 65535) return false;
-    t.n_tiles = t.tiles_x * t.tiles_y;
-    int bits = 1;
-    while ((1ll << bits) < t.n_tiles) ++bits;
-    t.tile_bits = bits;
-    return t.tile_bits + t.depth_bits <= 32;
+    return shape_ok && t.depth_bits == 0;
 }
 
-htgs_status make_layout(int64_t n, const htgs_camera *cam, const htgs_params *prm,
-                        const htgs_launch *launch, int64_t capacity, Layout &L) {
-    if (!cam || !prm || n < 0 || n > kMaxGaussians || capacity < 0 || capacity > kMaxCapacity)
-        return HTGS_ERR_INVALID_ARG;
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > (1 << 20) || cam->height > (1 << 20))
-        return HTGS_ERR_INVALID_ARG;
-    if (prm->K < 0) return HTGS_ERR_INVALID_ARG;
+bool camera_ok(const htgs_camera *cam) {
+    return cam && cam->width > 0 && cam->height > 0 && cam->width <= (1 << 20) && cam->height <= (1 << 20);
+}
+
+htgs_status params_ok(const htgs_params *prm, const htgs_launch *launch) {
+    if (!prm || prm->K < 0) return HTGS_ERR_INVALID_ARG;
     if (prm->K > HTGS_MAX_K) return HTGS_ERR_NOT_SUPPORTED;
     if (!(prm->tau_alpha > 0.f) || !(prm->alpha_max < 1.f) || !(prm->alpha_max > 0.f))
         return HTGS_ERR_INVALID_ARG;
     if (launch && (launch->px_per_thread < 0 || launch->px_per_thread > 4)) return HTGS_ERR_INVALID_ARG;
-    if (!make_tiles(cam, launch, L.tiles)) return HTGS_ERR_NOT_SUPPORTED;
-    L.n_blocks = (int)((n + kPreThreads - 1) / kPreThreads);
+    return HTGS_OK;
+}
+
+// The host-side description of a batch: per view its Gaussian count and camera.
+struct HostView {
+    int64_t n;
+    const htgs_camera *cam;
+};
+
+htgs_status make_layout(int n_views, const HostView *views, const htgs_params *prm, const htgs_launch *launch,
+                        int64_t capacity, Layout &L) {
+    if (n_views < 1 || n_views > kMaxViews || capacity < 0 || capacity > kMaxCapacity)
+        return HTGS_ERR_INVALID_ARG;
+    htgs_status st = params_ok(prm, launch);
+    if (st) return st;
+    if (!tile_shape(launch, L.tiles)) return HTGS_ERR_NOT_SUPPORTED;
+    int64_t n_rec = 0, n_tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (!camera_ok(views[v].cam) || views[v].n < 0) return HTGS_ERR_INVALID_ARG;
+        const int64_t tx = (views[v].cam->width + L.tiles.tile_w - 1) / L.tiles.tile_w;
+        const int64_t ty = (views[v].cam->height + L.tiles.tile_h - 1) / L.tiles.tile_h;
+        if (tx > 65535 || ty > 65535) return HTGS_ERR_NOT_SUPPORTED;
+        n_rec += views[v].n;
+        n_tiles += tx * ty;
+    }
+    if (n_rec > kMaxRecords || n_tiles > (1ll << 30)) return HTGS_ERR_INVALID_ARG;
+    L.n_rec = n_rec;
+    L.tiles.n_tiles = (int)n_tiles;
+    L.tiles.tiles_x = 0;
+    L.tiles.tiles_y = 0;
+    int bits = 1;
+    while ((1ll << bits) < n_tiles) ++bits;
+    L.tiles.tile_bits = bits;
+    L.n_blocks = (int)((n_rec + kPreThreads - 1) / kPreThreads);
     L.n_sort_blocks = (int)((capacity + kSortTile - 1) / kSortTile);
     if (L.n_sort_blocks < 1) L.n_sort_blocks = 1;
-    L.passes = (L.tiles.tile_bits + L.tiles.depth_bits + kRadixBits - 1) / kRadixBits;
+    L.passes = (bits + kRadixBits - 1) / kRadixBits;
     size_t o = 0;
     // Zero-initialised region (one memset per render).
     L.status = o; o = align_up(o + kStSlots * sizeof(int));
     L.stats = o; o = align_up(o + kStatSlots * sizeof(unsigned long long));
     L.total = o; o = align_up(o + 4 * sizeof(uint32_t));
+    L.work = o; o = align_up(o + 4 * sizeof(uint32_t));
     L.ghist = o; o = align_up(o + kMaxPasses * kRadix * sizeof(uint32_t));
     L.tickets = o; o = align_up(o + kMaxPasses * sizeof(uint32_t));
-    L.ranges = o; o = align_up(o + (size_t)L.tiles.n_tiles * sizeof(uint2));
+    L.ranges = o; o = align_up(o + (size_t)n_tiles * sizeof(uint2));
     L.lookback = o; o = align_up(o + (size_t)L.passes * L.n_sort_blocks * kRadix * sizeof(uint32_t));
     L.zero_end = o;
-    L.rec = o; o = align_up(o + (size_t)n * kRecF4 * sizeof(float4));
-    L.rect = o; o = align_up(o + (size_t)n * sizeof(uint2));
-    L.count = o; o = align_up(o + (size_t)n * sizeof(uint32_t));
+    L.rec = o; o = align_up(o + (size_t)n_rec * kRecF4 * sizeof(float4));
+    L.rect = o; o = align_up(o + (size_t)n_rec * sizeof(uint2));
+    L.count = o; o = align_up(o + (size_t)n_rec * sizeof(uint32_t));
     L.block_sums = o; o = align_up(o + (size_t)(L.n_blocks + 1) * sizeof(uint32_t));
     L.keys0 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.vals0 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.keys1 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.vals1 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
-    L.acc = o; o = align_up(o + (size_t)n * 16 * sizeof(float));
+    L.bwd_work = o; o = align_up(o + 4 * sizeof(uint32_t));
+    L.acc = o; o = align_up(o + (size_t)n_rec * 16 * sizeof(float));
     L.end = o;
-    L.saved_floats = (size_t)(7 + prm->K) * cam->width * cam->height;
     return HTGS_OK;
 }
 
@@ -125,6 +155,218 @@ void mark(const htgs_launch *launch, int idx, cudaStream_t s) {
     if (launch && launch->events[idx]) cudaEventRecord(static_cast<cudaEvent_t>(launch->events[idx]), s);
 }
 
+htgs_status collect(int n_views, const htgs_view *views, HostView *hv) {
+    if (!views || n_views < 1 || n_views > kMaxViews) return HTGS_ERR_INVALID_ARG;
+    for (int v = 0; v < n_views; ++v) {
+        htgs_status st = check_gaussians(views[v].gaussians);
+        if (st) return st;
+        hv[v].n = views[v].gaussians->n;
+        hv[v].cam = &views[v].camera;
+    }
+    return HTGS_OK;
+}
+
+// The device-side batch descriptor (passed by value to the kernels).
+void make_batch(int n_views, const htgs_view *views, const Layout &L, bool backward, Batch &b) {
+    memset(&b, 0, sizeof(b));
+    b.n_views = n_views;
+    b.n_rec = L.n_rec;
+    b.total_tiles = L.tiles.n_tiles;
+    long long rec = 0;
+    int tile = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const htgs_view &hv = views[v];
+        ViewDesc &d = b.v[v];
+        make_cam(&hv.camera, d.cam);
+        const htgs_gaussians *g = hv.gaussians;
+        d.means = g->means; d.log_scales = g->log_scales; d.quats = g->quats;
+        d.logits = g->opacity_logits; d.sh = g->sh;
+        d.n = g->n;
+        d.sh_degree = g->sh_degree;
+        d.rec_off = rec;
+        d.tile_off = tile;
+        d.tiles_x = (hv.camera.width + L.tiles.tile_w - 1) / L.tiles.tile_w;
+        d.tiles_y = (hv.camera.height + L.tiles.tile_h - 1) / L.tiles.tile_h;
+        d.image = hv.image;
+        d.saved = hv.saved;
+        if (backward) {
+            d.dl_dimg = hv.dl_dimage;
+            d.g_means = hv.grads->means; d.g_log_scales = hv.grads->log_scales;
+            d.g_quats = hv.grads->quats; d.g_logits = hv.grads->opacity_logits; d.g_sh = hv.grads->sh;
+        }
+        rec += g->n;
+        tile += d.tiles_x * d.tiles_y;
+    }
+}
+
+htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params *params,
+                         const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                         int64_t capacity, void *stream) {
+    HostView hv[kMaxViews];
+    htgs_status st = collect(n_views, views, hv);
+    if (st) return st;
+    if (!workspace || ((uintptr_t)workspace % kAlign)) return HTGS_ERR_INVALID_ARG;
+    for (int v = 0; v < n_views; ++v)
+        if (!views[v].image) return HTGS_ERR_INVALID_ARG;
+    Layout L;
+    st = make_layout(n_views, hv, params, launch, capacity, L);
+    if (st) return st;
+    if (workspace_bytes < L.end) return HTGS_ERR_WORKSPACE;
+    static thread_local Batch b; // large; built on the host per call
+    make_batch(n_views, views, L, false, b);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    if (cudaMemsetAsync(workspace, 0, L.zero_end, s) != cudaSuccess) return HTGS_ERR_CUDA;
+
+    ParamArgs pa;
+    make_prm(params, pa);
+    int *status = at<int>(workspace, L.status);
+    uint32_t *total = at<uint32_t>(workspace, L.total);
+
+    mark(launch, 0, s);
+    if (L.n_blocks > 0) {
+        PreArgs pre{};
+        pre.prm = pa; pre.tiles = L.tiles;
+        pre.rec = at<float4>(workspace, L.rec);
+        pre.rect = at<uint2>(workspace, L.rect);
+        pre.count = at<uint32_t>(workspace, L.count);
+        pre.block_sums = at<uint32_t>(workspace, L.block_sums);
+        pre.stats = at<unsigned long long>(workspace, L.stats);
+        preprocess_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(b, pre);
+    }
+    mark(launch, 1, s);
+    mark(launch, 2, s);
+    BinArgs bin{};
+    bin.n = L.n_rec; bin.n_blocks = L.n_blocks;
+    bin.rect = at<uint2>(workspace, L.rect);
+    bin.count = at<uint32_t>(workspace, L.count);
+    bin.block_sums = at<uint32_t>(workspace, L.block_sums);
+    bin.status = status; bin.capacity = capacity;
+    bin.keys = at<uint32_t>(workspace, L.keys0);
+    bin.vals = at<uint32_t>(workspace, L.vals0);
+    bin.total = total;
+    launch_scan_blocks(bin, s);
+    launch_emit(b, bin, s);
+
+    SortArgs so{};
+    so.capacity = capacity; so.total = total; so.passes = L.passes;
+    so.keys[0] = at<uint32_t>(workspace, L.keys0); so.vals[0] = at<uint32_t>(workspace, L.vals0);
+    so.keys[1] = at<uint32_t>(workspace, L.keys1); so.vals[1] = at<uint32_t>(workspace, L.vals1);
+    so.ghist = at<uint32_t>(workspace, L.ghist);
+    so.lookback = at<uint32_t>(workspace, L.lookback);
+    so.tickets = at<uint32_t>(workspace, L.tickets);
+    so.n_sort_blocks = L.n_sort_blocks; so.status = status;
+    const int sb = launch_sort(so, s);
+
+    RangeArgs ra{};
+    ra.total = total; ra.keys = so.keys[sb];
+    ra.ranges = at<uint2>(workspace, L.ranges); ra.n_tiles = L.tiles.n_tiles;
+    launch_ranges(ra, s);
+
+    BlendFwdArgs ba{};
+    ba.rec = at<float4>(workspace, L.rec);
+    ba.vals = so.vals[sb];
+    ba.ranges = at<uint2>(workspace, L.ranges);
+    ba.status = status;
+    ba.work = at<unsigned int>(workspace, L.work);
+    ba.tiles = L.tiles; ba.prm = pa;
+    ba.stats = at<unsigned long long>(workspace, L.stats);
+    const int ppt = (launch && launch->px_per_thread) ? launch->px_per_thread : 1;
+    mark(launch, 3, s);
+    mark(launch, 4, s);
+    if (!launch_blend_fwd(b, ba, ppt, s)) return HTGS_ERR_NOT_SUPPORTED;
+    mark(launch, 5, s);
+    return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
+}
+
+htgs_status render_batch_backward(int n_views, const htgs_view *views, const htgs_params *params,
+                                  const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                                  int64_t capacity, void *stream) {
+    HostView hv[kMaxViews];
+    htgs_status st = collect(n_views, views, hv);
+    if (st) return st;
+    if (!workspace || ((uintptr_t)workspace % kAlign)) return HTGS_ERR_INVALID_ARG;
+    for (int v = 0; v < n_views; ++v) {
+        const htgs_view &w = views[v];
+        const htgs_gaussians_grad *gr = w.grads;
+        if (!w.saved || !w.dl_dimage || !gr) return HTGS_ERR_INVALID_ARG;
+        if (w.gaussians->n > 0 && (!gr->means || !gr->log_scales || !gr->quats || !gr->opacity_logits || !gr->sh))
+            return HTGS_ERR_INVALID_ARG;
+    }
+    Layout L;
+    st = make_layout(n_views, hv, params, launch, capacity, L);
+    if (st) return st;
+    if (workspace_bytes < L.end) return HTGS_ERR_WORKSPACE;
+    static thread_local Batch b;
+    make_batch(n_views, views, L, true, b);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    // Views that share gradient buffers (several views of one scene) add
+    // into them; those buffers start from zero.
+    bool accumulate = false;
+    for (int v = 0; v < n_views && !accumulate; ++v)
+        for (int u = 0; u < v; ++u)
+            if (views[u].grads->means == views[v].grads->means) { accumulate = true; break; }
+    if (accumulate) {
+        for (int v = 0; v < n_views; ++v) {
+            bool first = true;
+            for (int u = 0; u < v; ++u)
+                if (views[u].grads->means == views[v].grads->means) first = false;
+            const int64_t n = views[v].gaussians->n;
+            if (!first || n == 0) continue;
+            const htgs_gaussians_grad *gr = views[v].grads;
+            const int nc = (views[v].gaussians->sh_degree + 1) * (views[v].gaussians->sh_degree + 1);
+            if (cudaMemsetAsync(gr->means, 0, (size_t)n * 3 * sizeof(float), s) != cudaSuccess ||
+                cudaMemsetAsync(gr->log_scales, 0, (size_t)n * 3 * sizeof(float), s) != cudaSuccess ||
+                cudaMemsetAsync(gr->quats, 0, (size_t)n * 4 * sizeof(float), s) != cudaSuccess ||
+                cudaMemsetAsync(gr->opacity_logits, 0, (size_t)n * sizeof(float), s) != cudaSuccess ||
+                cudaMemsetAsync(gr->sh, 0, (size_t)n * nc * 3 * sizeof(float), s) != cudaSuccess)
+                return HTGS_ERR_CUDA;
+        }
+    }
+    // Gradient accumulators and the persistent kernel's work counter.
+    if (cudaMemsetAsync(at<char>(workspace, L.bwd_work), 0, L.end - L.bwd_work, s) != cudaSuccess)
+        return HTGS_ERR_CUDA;
+    ParamArgs pa;
+    make_prm(params, pa);
+    const int sb = sorted_buffer(L);
+    float *acc = at<float>(workspace, L.acc);
+
+    BlendBwdArgs bb{};
+    bb.rec = at<float4>(workspace, L.rec);
+    bb.vals = at<uint32_t>(workspace, sb ? L.vals1 : L.vals0);
+    bb.ranges = at<uint2>(workspace, L.ranges);
+    bb.status = at<int>(workspace, L.status);
+    bb.work = at<unsigned int>(workspace, L.bwd_work);
+    bb.tiles = L.tiles; bb.prm = pa;
+    bb.acc = acc;
+    mark(launch, 0, s);
+    if (!launch_blend_bwd(b, bb, s)) return HTGS_ERR_NOT_SUPPORTED;
+    mark(launch, 1, s);
+    mark(launch, 2, s);
+    if (L.n_blocks > 0) {
+        PreBwdArgs pb{};
+        pb.prm = pa;
+        pb.rec = at<float4>(workspace, L.rec);
+        pb.rect = at<uint2>(workspace, L.rect);
+        pb.acc = acc;
+        pb.accumulate = accumulate ? 1 : 0;
+        preprocess_backward_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(b, pb);
+    }
+    mark(launch, 3, s);
+    return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
+}
+
+htgs_view single_view(const htgs_gaussians *g, const htgs_camera *cam, float *image, float *saved) {
+    htgs_view v;
+    memset(&v, 0, sizeof(v));
+    v.gaussians = g;
+    if (cam) v.camera = *cam;
+    v.image = image;
+    v.saved = saved;
+    return v;
+}
+
 } // namespace
 
 } // namespace htgs
@@ -149,19 +391,35 @@ const char *htgs_status_string(htgs_status s) {
 htgs_status htgs_workspace_size(int64_t n_gaussians, const htgs_camera *cam, const htgs_params *params,
                                 const htgs_launch *launch, int64_t instance_capacity, size_t *fwd_bytes,
                                 size_t *saved_bytes) {
+    if (!camera_ok(cam)) return HTGS_ERR_INVALID_ARG;
+    HostView hv{n_gaussians, cam};
     Layout L;
-    htgs_status st = make_layout(n_gaussians, cam, params, launch, instance_capacity, L);
+    htgs_status st = make_layout(1, &hv, params, launch, instance_capacity, L);
     if (st) return st;
     if (fwd_bytes) *fwd_bytes = L.end;
-    if (saved_bytes) *saved_bytes = L.saved_floats * sizeof(float);
+    if (saved_bytes) *saved_bytes = (size_t)(7 + params->K) * cam->width * cam->height * sizeof(float);
+    return HTGS_OK;
+}
+
+htgs_status htgs_batch_workspace_size(int32_t n_views, const htgs_view *views, const htgs_params *params,
+                                      const htgs_launch *launch, int64_t instance_capacity,
+                                      size_t *workspace_bytes) {
+    HostView hv[kMaxViews];
+    htgs_status st = collect(n_views, views, hv);
+    if (st) return st;
+    Layout L;
+    st = make_layout(n_views, hv, params, launch, instance_capacity, L);
+    if (st) return st;
+    if (workspace_bytes) *workspace_bytes = L.end;
     return HTGS_OK;
 }
 
 htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam, const htgs_params *params,
                                   const htgs_launch *launch, int64_t instance_capacity, htgs_layout *out) {
-    if (!out) return HTGS_ERR_INVALID_ARG;
+    if (!out || !camera_ok(cam)) return HTGS_ERR_INVALID_ARG;
+    HostView hv{n_gaussians, cam};
     Layout L;
-    htgs_status st = make_layout(n_gaussians, cam, params, launch, instance_capacity, L);
+    htgs_status st = make_layout(1, &hv, params, launch, instance_capacity, L);
     if (st) return st;
     const int sb = sorted_buffer(L);
     out->rec = L.rec;
@@ -172,8 +430,8 @@ htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam, c
     out->ranges = L.ranges;
     out->acc = L.acc;
     out->n_tiles = L.tiles.n_tiles;
-    out->tiles_x = L.tiles.tiles_x;
-    out->tiles_y = L.tiles.tiles_y;
+    out->tiles_x = (cam->width + L.tiles.tile_w - 1) / L.tiles.tile_w;
+    out->tiles_y = (cam->height + L.tiles.tile_h - 1) / L.tiles.tile_h;
     out->tile_bits = L.tiles.tile_bits;
     return HTGS_OK;
 }
@@ -181,138 +439,33 @@ htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam, c
 htgs_status htgs_render(const htgs_gaussians *g, const htgs_camera *cam, const htgs_params *params,
                         const htgs_launch *launch, void *workspace, size_t workspace_bytes,
                         int64_t instance_capacity, float *saved, float *image, void *stream) {
-    htgs_status st = check_gaussians(g);
-    if (st) return st;
-    if (!image || !workspace || ((uintptr_t)workspace % kAlign)) return HTGS_ERR_INVALID_ARG;
-    Layout L;
-    st = make_layout(g->n, cam, params, launch, instance_capacity, L);
-    if (st) return st;
-    if (workspace_bytes < L.end) return HTGS_ERR_WORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaGetLastError();
-    if (cudaMemsetAsync(workspace, 0, L.zero_end, s) != cudaSuccess) return HTGS_ERR_CUDA;
-
-    CamArgs ca;
-    make_cam(cam, ca);
-    ParamArgs pa;
-    make_prm(params, pa);
-    int *status = at<int>(workspace, L.status);
-    uint32_t *total = at<uint32_t>(workspace, L.total);
-
-    mark(launch, 0, s);
-    if (L.n_blocks > 0) {
-        PreArgs pre{};
-        pre.means = g->means; pre.log_scales = g->log_scales; pre.quats = g->quats;
-        pre.logits = g->opacity_logits; pre.sh = g->sh;
-        pre.n = g->n; pre.sh_degree = g->sh_degree;
-        pre.cam = ca; pre.prm = pa; pre.tiles = L.tiles;
-        pre.rec = at<float4>(workspace, L.rec);
-        pre.rect = at<uint2>(workspace, L.rect);
-        pre.count = at<uint32_t>(workspace, L.count);
-        pre.block_sums = at<uint32_t>(workspace, L.block_sums);
-        pre.stats = at<unsigned long long>(workspace, L.stats);
-        preprocess_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(pre);
-    }
-    mark(launch, 1, s);
-    mark(launch, 2, s);
-    BinArgs bin{};
-    bin.n = g->n; bin.n_blocks = L.n_blocks;
-    bin.rect = at<uint2>(workspace, L.rect);
-    bin.count = at<uint32_t>(workspace, L.count);
-    bin.block_sums = at<uint32_t>(workspace, L.block_sums);
-    bin.status = status; bin.capacity = instance_capacity; bin.tiles = L.tiles;
-    bin.keys = at<uint32_t>(workspace, L.keys0);
-    bin.vals = at<uint32_t>(workspace, L.vals0);
-    bin.total = total;
-    launch_scan_blocks(bin, s);
-    launch_emit(bin, s);
-
-    SortArgs so{};
-    so.capacity = instance_capacity; so.total = total; so.passes = L.passes;
-    so.keys[0] = at<uint32_t>(workspace, L.keys0); so.vals[0] = at<uint32_t>(workspace, L.vals0);
-    so.keys[1] = at<uint32_t>(workspace, L.keys1); so.vals[1] = at<uint32_t>(workspace, L.vals1);
-    so.ghist = at<uint32_t>(workspace, L.ghist);
-    so.lookback = at<uint32_t>(workspace, L.lookback);
-    so.tickets = at<uint32_t>(workspace, L.tickets);
-    so.n_sort_blocks = L.n_sort_blocks; so.status = status;
-    const int sb = launch_sort(so, s);
-
-    RangeArgs ra{};
-    ra.total = total; ra.keys = so.keys[sb]; ra.shift = L.tiles.depth_bits;
-    ra.ranges = at<uint2>(workspace, L.ranges); ra.capacity = instance_capacity;
-    launch_ranges(ra, L.tiles.n_tiles, s);
-
-    BlendFwdArgs ba{};
-    ba.rec = at<float4>(workspace, L.rec);
-    ba.vals = so.vals[sb];
-    ba.ranges = at<uint2>(workspace, L.ranges);
-    ba.status = status; ba.tiles = L.tiles; ba.prm = pa;
-    ba.width = cam->width; ba.height = cam->height;
-    ba.image = image; ba.saved = saved;
-    ba.stats = at<unsigned long long>(workspace, L.stats);
-    const int ppt = (launch && launch->px_per_thread) ? launch->px_per_thread : 1;
-    mark(launch, 3, s);
-    mark(launch, 4, s);
-    if (!launch_blend_fwd(ba, ppt, s)) return HTGS_ERR_NOT_SUPPORTED;
-    mark(launch, 5, s);
-    return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
+    if (!camera_ok(cam)) return HTGS_ERR_INVALID_ARG;
+    const htgs_view v = single_view(g, cam, image, saved);
+    return render_batch(1, &v, params, launch, workspace, workspace_bytes, instance_capacity, stream);
 }
 
 htgs_status htgs_render_backward(const htgs_gaussians *g, const htgs_camera *cam,
                                  const htgs_params *params, const htgs_launch *launch, void *workspace,
                                  size_t workspace_bytes, int64_t instance_capacity, const float *saved,
                                  const float *dl_dimage, const htgs_gaussians_grad *grads, void *stream) {
-    htgs_status st = check_gaussians(g);
-    if (st) return st;
-    if (!workspace || ((uintptr_t)workspace % kAlign) || !saved || !dl_dimage || !grads)
-        return HTGS_ERR_INVALID_ARG;
-    if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
-                     !grads->sh))
-        return HTGS_ERR_INVALID_ARG;
-    Layout L;
-    st = make_layout(g->n, cam, params, launch, instance_capacity, L);
-    if (st) return st;
-    if (workspace_bytes < L.end) return HTGS_ERR_WORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaGetLastError();
-    float *acc = at<float>(workspace, L.acc);
-    if (g->n > 0 && cudaMemsetAsync(acc, 0, (size_t)g->n * 16 * sizeof(float), s) != cudaSuccess)
-        return HTGS_ERR_CUDA;
-    ParamArgs pa;
-    make_prm(params, pa);
-    CamArgs ca;
-    make_cam(cam, ca);
-    const int sb = sorted_buffer(L);
+    if (!camera_ok(cam)) return HTGS_ERR_INVALID_ARG;
+    htgs_view v = single_view(g, cam, nullptr, const_cast<float *>(saved));
+    v.dl_dimage = dl_dimage;
+    v.grads = grads;
+    return render_batch_backward(1, &v, params, launch, workspace, workspace_bytes, instance_capacity, stream);
+}
 
-    BlendBwdArgs bb{};
-    bb.rec = at<float4>(workspace, L.rec);
-    bb.vals = at<uint32_t>(workspace, sb ? L.vals1 : L.vals0);
-    bb.ranges = at<uint2>(workspace, L.ranges);
-    bb.status = at<int>(workspace, L.status);
-    bb.tiles = L.tiles; bb.prm = pa;
-    bb.width = cam->width; bb.height = cam->height;
-    bb.saved = saved; bb.dl_dimg = dl_dimage; bb.acc = acc; bb.n = g->n;
-    const int ppt = (launch && launch->px_per_thread) ? launch->px_per_thread : 2;
-    mark(launch, 0, s);
-    if (!launch_blend_bwd(bb, ppt, s)) return HTGS_ERR_NOT_SUPPORTED;
-    mark(launch, 1, s);
-    mark(launch, 2, s);
+htgs_status htgs_render_batch(int32_t n_views, const htgs_view *views, const htgs_params *params,
+                              const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                              int64_t instance_capacity, void *stream) {
+    return render_batch(n_views, views, params, launch, workspace, workspace_bytes, instance_capacity, stream);
+}
 
-    if (L.n_blocks > 0) {
-        PreBwdArgs pb{};
-        pb.means = g->means; pb.log_scales = g->log_scales; pb.quats = g->quats;
-        pb.logits = g->opacity_logits; pb.sh = g->sh;
-        pb.n = g->n; pb.sh_degree = g->sh_degree;
-        pb.cam = ca; pb.prm = pa;
-        pb.rec = at<float4>(workspace, L.rec);
-        pb.rect = at<uint2>(workspace, L.rect);
-        pb.acc = acc;
-        pb.g_means = grads->means; pb.g_log_scales = grads->log_scales; pb.g_quats = grads->quats;
-        pb.g_logits = grads->opacity_logits; pb.g_sh = grads->sh;
-        preprocess_backward_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(pb);
-    }
-    mark(launch, 3, s);
-    return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
+htgs_status htgs_render_batch_backward(int32_t n_views, const htgs_view *views, const htgs_params *params,
+                                       const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                                       int64_t instance_capacity, void *stream) {
+    return render_batch_backward(n_views, views, params, launch, workspace, workspace_bytes, instance_capacity,
+                                 stream);
 }
 
 htgs_status htgs_get_error(void *workspace, size_t workspace_bytes, void *stream, htgs_status *status,

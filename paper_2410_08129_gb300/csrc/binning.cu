@@ -89,12 +89,19 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(BinArgs a) {
 // ---------------------------------------------------------------------------
 // Emit: instance j of Gaussian g covers tile (tx0 + r % w, ty0 + r / w).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPreThreads) emit_kernel(BinArgs a) {
+__global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant__ Batch b, BinArgs a) {
     __shared__ uint32_t warp_tot[kPreThreads / 32];
     if (a.status[kStError] == HTGS_ERR_OVERFLOW) return;
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t c = i < a.n ? a.count[i] : 0u;
+    // The record's view: its tile numbering (row length and first global tile).
+    uint32_t vtx = 0, vtoff = 0;
+    if (c) {
+        const ViewDesc &V = b.v[view_of_record(b, i)];
+        vtx = (uint32_t)V.tiles_x;
+        vtoff = (uint32_t)V.tile_off;
+    }
     uint32_t incl = c;
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t t = __shfl_up_sync(kFull, incl, o);
@@ -123,6 +130,8 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(BinArgs a) {
         const uint32_t rx = __shfl_sync(kFull, r.x, L);
         const uint32_t ry = __shfl_sync(kFull, r.y, L);
         const uint32_t eL = __shfl_sync(kFull, excl, L);
+        const uint32_t ltx = __shfl_sync(kFull, vtx, L);
+        const uint32_t ltoff = __shfl_sync(kFull, vtoff, L);
         if (j < wtot) {
             const uint32_t rr = j - eL;
             const uint32_t tx0 = rx & 0xffffu, tx1 = rx >> 16;
@@ -131,7 +140,7 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(BinArgs a) {
             const uint32_t ty = (ry & 0xffffu) + rr / w;
             const uint64_t pos = base + j;
             if (pos < (uint64_t)a.capacity) {
-                a.keys[pos] = (ty * (uint32_t)a.tiles.tiles_x + tx) << a.tiles.depth_bits;
+                a.keys[pos] = ltoff + ty * ltx + tx;
                 a.vals[pos] = gid0 + (uint32_t)L;
             }
         }
@@ -288,10 +297,10 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
 __global__ void ranges_kernel(RangeArgs a) {
     const uint32_t total = *a.total;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const uint32_t t = a.keys[i] >> a.shift;
+        const uint32_t t = a.keys[i];
         if (t >= (uint32_t)a.n_tiles) continue;
-        if (i == 0 || (a.keys[i - 1] >> a.shift) != t) a.ranges[t].x = i;
-        if (i + 1 == total || (a.keys[i + 1] >> a.shift) != t) a.ranges[t].y = i + 1;
+        if (i == 0 || a.keys[i - 1] != t) a.ranges[t].x = i;
+        if (i + 1 == total || a.keys[i + 1] != t) a.ranges[t].y = i + 1;
     }
 }
 
@@ -301,8 +310,8 @@ void launch_scan_blocks(const BinArgs &a, cudaStream_t s) {
     scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(a);
 }
 
-void launch_emit(const BinArgs &a, cudaStream_t s) {
-    if (a.n_blocks > 0) emit_kernel<<<a.n_blocks, kPreThreads, 0, s>>>(a);
+void launch_emit(const Batch &b, const BinArgs &a, cudaStream_t s) {
+    if (a.n_blocks > 0) emit_kernel<<<a.n_blocks, kPreThreads, 0, s>>>(b, a);
 }
 
 int launch_sort(const SortArgs &a, cudaStream_t s) {
@@ -319,13 +328,22 @@ int launch_sort(const SortArgs &a, cudaStream_t s) {
     return src;
 }
 
-void launch_ranges(RangeArgs a, int n_tiles, cudaStream_t s) {
-    a.n_tiles = n_tiles;
+void launch_ranges(RangeArgs a, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ranges_kernel<<<sms * 8, 256, 0, s>>>(a);
-    (void)n_tiles;
+}
+
+int persistent_grid(const void *kernel, int threads, size_t dyn_smem, int items) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long grid = (long long)sms * per_sm;
+    return (int)(grid < items ? grid : (items > 0 ? items : 1));
 }
 
 } // namespace htgs

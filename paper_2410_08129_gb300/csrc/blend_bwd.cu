@@ -1,5 +1,6 @@
-// blend_bwd.cu -- the blend adjoint (instantiation unit): one kernel per tile
-// shape, core size at run time, per-pixel state in dynamic shared memory.
+// blend_bwd.cu -- the blend adjoint (instantiation unit): one persistent
+// kernel per tile shape, core size at run time, per-pixel state in dynamic
+// shared memory.
 #include "blend_impl.cuh"
 
 namespace htgs {
@@ -7,7 +8,7 @@ namespace htgs {
 namespace {
 
 template <int TW, int TH>
-bool run_bwd(const BlendBwdArgs &a, cudaStream_t s) {
+bool run_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     const size_t smem = bwd_smem_bytes(TW * TH, a.prm.K);
     // Raise the dynamic shared-memory limit once per process and device.
     static bool configured = false;
@@ -17,19 +18,19 @@ bool run_bwd(const BlendBwdArgs &a, cudaStream_t s) {
             return false;
         configured = true;
     }
-    blend_bwd_kernel<TW, TH><<<a.tiles.n_tiles, kBwdThreads, smem, s>>>(a);
+    const int grid = persistent_grid((const void *)blend_bwd_kernel<TW, TH>, kBwdThreads, smem, b.total_tiles);
+    blend_bwd_kernel<TW, TH><<<grid, kBwdThreads, smem, s>>>(b, a);
     return true;
 }
 
 } // namespace
 
-bool launch_blend_bwd(const BlendBwdArgs &a, int ppt, cudaStream_t s) {
-    (void)ppt;
+bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     if (a.prm.K < 0 || a.prm.K > HTGS_MAX_K) return false;
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
-    if (tw == 16 && th == 16) return run_bwd<16, 16>(a, s);
-    if (tw == 16 && th == 8) return run_bwd<16, 8>(a, s);
-    if (tw == 8 && th == 8) return run_bwd<8, 8>(a, s);
+    if (tw == 16 && th == 16) return run_bwd<16, 16>(b, a, s);
+    if (tw == 16 && th == 8) return run_bwd<16, 8>(b, a, s);
+    if (tw == 8 && th == 8) return run_bwd<8, 8>(b, a, s);
     return false;
 }
 

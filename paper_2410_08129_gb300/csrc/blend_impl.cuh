@@ -78,17 +78,29 @@ __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KM
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT, (PPT == 1 && KMAX <= 8) ? 1024 / (TW * TH / PPT) : 1)
-blend_fwd_kernel(BlendFwdArgs a) {
+blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
     constexpr int WPR = TW / 8;  // footprints per tile row
     static_assert(TW % 8 == 0 && TH % WY == 0 && NT % 32 == 0, "unsupported blend shape");
     __shared__ float4 s_rec[2][kBatch][kRecF4];
     __shared__ uint32_t s_gid[2][kBatch];
+    __shared__ int s_item;
     if (a.status[kStError] != 0) return;
 
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles.tiles_x, ty = tile / a.tiles.tiles_x;
+    // Persistent CTA: take (view, tile) items from the shared queue.
+    for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+    __syncthreads();
+    const int tile = s_item;
+    __syncthreads();
+    if (tile >= bt.total_tiles) break;
+    const ViewDesc &view = bt.v[view_of_tile(bt, tile)];
+    const int local = tile - view.tile_off;
+    const int tx = local % view.tiles_x, ty = local / view.tiles_x;
+    const int width = view.cam.width, height = view.cam.height;
+    float *const image = view.image;
+    float *const saved = view.saved;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wx0 = tx * TW + (warp % WPR) * 8;
     const int wy0 = ty * TH + (warp / WPR) * WY;
@@ -213,7 +225,7 @@ blend_fwd_kernel(BlendFwdArgs a) {
         unsigned long long kept = 0;
 #pragma unroll
         for (int p = 0; p < PPT; ++p)
-            if (px_i < a.width && py_i0 + p < a.height) kept += (unsigned)nall[p];
+            if (px_i < width && py_i0 + p < height) kept += (unsigned)nall[p];
         unsigned long long adm = n_adm, ins = n_ins;
         for (int o = 16; o > 0; o >>= 1) {
             kept += __shfl_xor_sync(0xffffffffu, kept, o);
@@ -229,12 +241,12 @@ blend_fwd_kernel(BlendFwdArgs a) {
 
     // Epilogue: composite the core front to back (Eq. (15)), recover the
     // tail sums and composite the tail behind it.
-    const size_t npix = (size_t)a.width * a.height;
+    const size_t npix = (size_t)width * height;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int x = px_i, y = py_i0 + p;
-        if (x >= a.width || y >= a.height) continue;
-        const size_t pix = (size_t)y * a.width + x;
+        if (x >= width || y >= height) continue;
+        const size_t pix = (size_t)y * width + x;
         float C[3] = {0.f, 0.f, 0.f};
         float T = 1.f, Ac = 0.f, Sc[3] = {0.f, 0.f, 0.f};
         int n_core = 0;
@@ -253,7 +265,7 @@ blend_fwd_kernel(BlendFwdArgs a) {
             Ac += al;
             Sc[0] += al * c5.x; Sc[1] += al * c5.y; Sc[2] += al * c5.z;
             T = __fmaf_rn(-T, al, T);
-            if (a.saved) a.saved[(size_t)(7 + n_core) * npix + pix] = __uint_as_float(gid);
+            if (saved) saved[(size_t)(7 + n_core) * npix + pix] = __uint_as_float(gid);
             ++n_core;
         }
         const int n_tail = nall[p] - n_core;
@@ -267,21 +279,22 @@ blend_fwd_kernel(BlendFwdArgs a) {
             Pc = fminf(sP[p], T);
         }
         const float wt = T - Pc;
-        float *img = a.image + pix * 3;
+        float *img = image + pix * 3;
         img[0] = C[0] + wt * ct[0] + Pc * a.prm.bg[0];
         img[1] = C[1] + wt * ct[1] + Pc * a.prm.bg[1];
         img[2] = C[2] + wt * ct[2] + Pc * a.prm.bg[2];
-        if (a.saved) {
-            a.saved[0 * npix + pix] = __int_as_float(n_core);
-            a.saved[1 * npix + pix] = T;
-            a.saved[2 * npix + pix] = Pc;
-            a.saved[3 * npix + pix] = At;
-            a.saved[4 * npix + pix] = ct[0];
-            a.saved[5 * npix + pix] = ct[1];
-            a.saved[6 * npix + pix] = ct[2];
-            for (int k = n_core; k < K; ++k) a.saved[(size_t)(7 + k) * npix + pix] = __uint_as_float(0xffffffffu);
+        if (saved) {
+            saved[0 * npix + pix] = __int_as_float(n_core);
+            saved[1 * npix + pix] = T;
+            saved[2 * npix + pix] = Pc;
+            saved[3 * npix + pix] = At;
+            saved[4 * npix + pix] = ct[0];
+            saved[5 * npix + pix] = ct[1];
+            saved[6 * npix + pix] = ct[2];
+            for (int k = n_core; k < K; ++k) saved[(size_t)(7 + k) * npix + pix] = __uint_as_float(0xffffffffu);
         }
     }
+    } // next item
 }
 
 // ---------------------------------------------------------------------------
@@ -322,13 +335,14 @@ __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(BlendBwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
     constexpr int TP = TW * TH;
     constexpr int NW = kBwdThreads / 32;
     extern __shared__ float4 smem[];
     __shared__ float4 s_wrec[NW][2][kRecF4];  // per-warp double-buffered record
     __shared__ uint32_t s_wgid[NW][2];
     __shared__ uint32_t s_next;
+    __shared__ int s_item;
     const int K = a.prm.K;
     float4 *s_pa = smem;                 // g.xyz, k0
     float4 *s_pb = s_pa + TP;            // u.xyz, k1
@@ -338,35 +352,47 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(BlendBwdArgs 
     float *s_cv = s_cw + (size_t)K * TP;                             // [K][TP] alpha_r T_r
     if (a.status[kStError] != 0) return;
 
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles.tiles_x, ty = tile / a.tiles.tiles_x;
+    // Persistent CTA: take (view, tile) items from the shared queue.
+    for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+    __syncthreads();
+    const int tile = s_item;
+    __syncthreads();
+    if (tile >= bt.total_tiles) break;
+    const ViewDesc &view = bt.v[view_of_tile(bt, tile)];
+    const int local = tile - view.tile_off;
+    const int tx = local % view.tiles_x, ty = local / view.tiles_x;
+    const int width = view.cam.width, height = view.cam.height;
+    const float *const saved = view.saved;
+    const float *const dl_dimg = view.dl_dimg;
+    const long long n_rec = bt.n_rec;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = tx * TW, y0 = ty * TH;
-    const int x1 = min(x0 + TW, a.width) - 1, y1 = min(y0 + TH, a.height) - 1;
+    const int x1 = min(x0 + TW, width) - 1, y1 = min(y0 + TH, height) - 1;
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
     const float bg0 = a.prm.bg[0], bg1 = a.prm.bg[1], bg2 = a.prm.bg[2];
-    const size_t npix = (size_t)a.width * a.height;
+    const size_t npix = (size_t)width * height;
     const uint2 range = a.ranges[tile];
 
     // Phase A: per-pixel adjoint state.
     for (int p = tid; p < TP; p += kBwdThreads) {
         const int x = x0 + p % TW, y = y0 + p / TW;
-        const bool inside = x < a.width && y < a.height;
-        const size_t pix = inside ? (size_t)y * a.width + x : 0;
+        const bool inside = x < width && y < height;
+        const size_t pix = inside ? (size_t)y * width + x : 0;
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         int n_core = 0;
         float Tc = 1.f, Pc = 1.f, At = 0.f, ct0 = 0.f, ct1 = 0.f, ct2 = 0.f;
         if (inside) {
-            g0 = a.dl_dimg[pix * 3 + 0];
-            g1 = a.dl_dimg[pix * 3 + 1];
-            g2 = a.dl_dimg[pix * 3 + 2];
-            n_core = min(max(__float_as_int(a.saved[0 * npix + pix]), 0), K);
-            Tc = a.saved[1 * npix + pix];
-            Pc = a.saved[2 * npix + pix];
-            At = a.saved[3 * npix + pix];
-            ct0 = a.saved[4 * npix + pix];
-            ct1 = a.saved[5 * npix + pix];
-            ct2 = a.saved[6 * npix + pix];
+            g0 = dl_dimg[pix * 3 + 0];
+            g1 = dl_dimg[pix * 3 + 1];
+            g2 = dl_dimg[pix * 3 + 2];
+            n_core = min(max(__float_as_int(saved[0 * npix + pix]), 0), K);
+            Tc = saved[1 * npix + pix];
+            Pc = saved[2 * npix + pix];
+            At = saved[3 * npix + pix];
+            ct0 = saved[4 * npix + pix];
+            ct1 = saved[5 * npix + pix];
+            ct2 = saved[6 * npix + pix];
         }
         float u0 = 0.f, u1 = 0.f, u2 = 0.f, k0 = 0.f, k1 = 0.f;
         if (At > 0.f) {
@@ -384,9 +410,9 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(BlendBwdArgs 
         uint32_t lastg = 0xffffffffu;
         // Back to front: u_r = g.(c_r - G_r) into s_cw, alpha_r into s_cv.
         for (int r = n_core - 1; r >= 0; --r) {
-            const uint32_t gid = __float_as_uint(a.saved[(size_t)(7 + r) * npix + pix]);
+            const uint32_t gid = __float_as_uint(saved[(size_t)(7 + r) * npix + pix]);
             float ur = 0.f, al = 0.f;
-            if ((int64_t)gid < a.n) {
+            if ((long long)gid < n_rec) {
                 const float4 *rr = a.rec + (size_t)gid * kRecF4;
                 const float4 c0 = rr[0], c1 = rr[1], c2 = rr[2], c4 = rr[4], c5 = rr[5];
                 const float ex = __fsub_rn((float)x + 0.5f, c4.z), ey = __fsub_rn((float)y + 0.5f, c4.w);
@@ -539,22 +565,26 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(BlendBwdArgs 
         slot ^= 1;
         j = jn;
     }
+    __syncthreads();  // the next item rebuilds the per-pixel state
+    } // next item
 }
 
 // ---------------------------------------------------------------------------
 // Dispatch over tile shape and pixels per thread for one KMAX.
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT>
-void run_fwd(const BlendFwdArgs &a, cudaStream_t s) {
-    blend_fwd_kernel<KMAX, TW, TH, PPT><<<a.tiles.n_tiles, TW * TH / PPT, 0, s>>>(a);
+void run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
+    constexpr int NT = TW * TH / PPT;
+    const int grid = persistent_grid((const void *)blend_fwd_kernel<KMAX, TW, TH, PPT>, NT, 0, b.total_tiles);
+    blend_fwd_kernel<KMAX, TW, TH, PPT><<<grid, NT, 0, s>>>(b, a);
 }
 
 template <int KMAX, int PPT>
-bool dispatch_shape_fwd(const BlendFwdArgs &a, cudaStream_t s) {
+bool dispatch_shape_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
-    if (tw == 16 && th == 16) { run_fwd<KMAX, 16, 16, PPT>(a, s); return true; }
-    if (tw == 16 && th == 8 && PPT <= 2) { run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2)>(a, s); return true; }
-    if (tw == 8 && th == 8 && PPT <= 2) { run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(a, s); return true; }
+    if (tw == 16 && th == 16) { run_fwd<KMAX, 16, 16, PPT>(b, a, s); return true; }
+    if (tw == 16 && th == 8 && PPT <= 2) { run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2)>(b, a, s); return true; }
+    if (tw == 8 && th == 8 && PPT <= 2) { run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(b, a, s); return true; }
     return false;
 }
 

@@ -3,10 +3,10 @@
 
 namespace htgs {
 
-bool blend_fwd_k16(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_fwd<16, 1>(a, s);
-    if (ppt == 2) return dispatch_shape_fwd<16, 2>(a, s);
-    return dispatch_shape_fwd<16, 1>(a, s);
+bool blend_fwd_k16(const Batch &b, const BlendFwdArgs &a, int ppt, cudaStream_t s) {
+    if (ppt == 1) return dispatch_shape_fwd<16, 1>(b, a, s);
+    if (ppt == 2) return dispatch_shape_fwd<16, 2>(b, a, s);
+    return dispatch_shape_fwd<16, 1>(b, a, s);
 }
 
 } // namespace htgs

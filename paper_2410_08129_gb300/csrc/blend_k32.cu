@@ -3,9 +3,9 @@
 
 namespace htgs {
 
-bool blend_fwd_k32(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_fwd<32, 1>(a, s);
-    return dispatch_shape_fwd<32, 1>(a, s);
+bool blend_fwd_k32(const Batch &b, const BlendFwdArgs &a, int ppt, cudaStream_t s) {
+    if (ppt == 1) return dispatch_shape_fwd<32, 1>(b, a, s);
+    return dispatch_shape_fwd<32, 1>(b, a, s);
 }
 
 } // namespace htgs

@@ -3,11 +3,11 @@
 
 namespace htgs {
 
-bool blend_fwd_k8(const BlendFwdArgs &a, int ppt, cudaStream_t s) {
-    if (ppt == 1) return dispatch_shape_fwd<8, 1>(a, s);
-    if (ppt == 2) return dispatch_shape_fwd<8, 2>(a, s);
-    if (ppt == 4) return dispatch_shape_fwd<8, 4>(a, s);
-    return dispatch_shape_fwd<8, 1>(a, s);
+bool blend_fwd_k8(const Batch &b, const BlendFwdArgs &a, int ppt, cudaStream_t s) {
+    if (ppt == 1) return dispatch_shape_fwd<8, 1>(b, a, s);
+    if (ppt == 2) return dispatch_shape_fwd<8, 2>(b, a, s);
+    if (ppt == 4) return dispatch_shape_fwd<8, 4>(b, a, s);
+    return dispatch_shape_fwd<8, 1>(b, a, s);
 }
 
 } // namespace htgs

@@ -1,5 +1,11 @@
 // kernels.cuh -- argument blocks and launch entry points of the kernels
 // behind the C ABI. Host code in api.cu is the only caller.
+//
+// Every render is a batch of views (a single-view render is a batch of one).
+// A view has its own camera, the scene it renders (several views may share
+// one scene) and its outputs. Records are indexed per (view, Gaussian): view
+// v owns records [rec_off, rec_off + n); tiles are numbered globally: view v
+// owns tiles [tile_off, tile_off + tiles_x * tiles_y).
 #pragma once
 
 #include "common.cuh"
@@ -13,44 +19,78 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
+constexpr int kMaxViews = HTGS_MAX_VIEWS;
+
+struct ViewDesc {
+    CamArgs cam;
+    const float *means, *log_scales, *quats, *logits, *sh;
+    float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+    float *image;          // H x W x 3
+    float *saved;          // (7 + K) planes of H*W, or nullptr
+    const float *dl_dimg;  // H x W x 3 (backward)
+    long long n;           // Gaussians of the scene
+    long long rec_off;     // first record of this view
+    int sh_degree;
+    int tile_off;          // first global tile of this view
+    int tiles_x, tiles_y;
+};
+
+// Passed by value (as a __grid_constant__ kernel parameter).
+struct Batch {
+    int n_views;
+    int total_tiles;
+    long long n_rec;
+    ViewDesc v[kMaxViews];
+};
+
+// View owning record i (records are grouped by view in increasing order).
+__device__ __forceinline__ int view_of_record(const Batch &b, long long i) {
+    int lo = 0, hi = b.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.v[mid].rec_off <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// View owning global tile t.
+__device__ __forceinline__ int view_of_tile(const Batch &b, int t) {
+    int lo = 0, hi = b.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.v[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 struct PreArgs {
-    const float *means, *log_scales, *quats, *logits, *sh;
-    int64_t n;
-    int sh_degree;
-    CamArgs cam;
     ParamArgs prm;
-    TileArgs tiles;
-    float4 *rec;          // n * 6
-    uint2 *rect;          // n: (tx0 | tx1 << 16, ty0 | ty1 << 16)
-    uint32_t *count;      // n
-    uint32_t *block_sums; // ceil(n / kPreThreads)
+    TileArgs tiles;        // tile shape (counts per view are in the batch)
+    float4 *rec;           // n_rec * kRecF4
+    uint2 *rect;           // n_rec: (tx0 | tx1 << 16, ty0 | ty1 << 16), view-local tiles
+    uint32_t *count;       // n_rec
+    uint32_t *block_sums;  // ceil(n_rec / kPreThreads)
     unsigned long long *stats;
 };
 
 struct PreBwdArgs {
-    const float *means, *log_scales, *quats, *logits, *sh;
-    int64_t n;
-    int sh_degree;
-    CamArgs cam;
     ParamArgs prm;
     const float4 *rec;
     const uint2 *rect;
-    const float *acc;     // n * 16
-    float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+    const float *acc;      // n_rec * 16
+    int accumulate;        // 1: several views share a scene, add into the gradients atomically
 };
 
 struct BinArgs {
-    int64_t n;
-    int n_blocks;               // ceil(n / kPreThreads)
+    long long n;           // records
+    int n_blocks;          // ceil(n / kPreThreads)
     const uint2 *rect;
     const uint32_t *count;
-    uint32_t *block_sums;       // in: per-block sums; out: exclusive block offsets
+    uint32_t *block_sums;  // in: per-block sums; out: exclusive block offsets
     int *status;
     int64_t capacity;
-    TileArgs tiles;
-    uint32_t *keys, *vals;      // emit targets
-    uint32_t *total;            // device copy of the instance count (clamped use)
+    uint32_t *keys, *vals; // emit targets: global tile id, record index
+    uint32_t *total;       // device copy of the instance count (0 on overflow)
 };
 
 struct SortArgs {
@@ -58,9 +98,9 @@ struct SortArgs {
     const uint32_t *total;
     int passes;
     uint32_t *keys[2], *vals[2];
-    uint32_t *ghist;            // kMaxPasses * kRadix
-    uint32_t *lookback;         // passes * n_sort_blocks * kRadix
-    uint32_t *tickets;          // kMaxPasses
+    uint32_t *ghist;       // kMaxPasses * kRadix
+    uint32_t *lookback;    // passes * n_sort_blocks * kRadix
+    uint32_t *tickets;     // kMaxPasses
     int n_sort_blocks;
     int *status;
 };
@@ -68,22 +108,18 @@ struct SortArgs {
 struct RangeArgs {
     const uint32_t *total;
     const uint32_t *keys;
-    int shift;                  // key >> shift = tile id
-    uint2 *ranges;              // n_tiles
-    int64_t capacity;
+    uint2 *ranges;         // total_tiles
     int n_tiles;
 };
 
 struct BlendFwdArgs {
     const float4 *rec;
-    const uint32_t *vals;       // sorted gids
+    const uint32_t *vals;  // sorted record indices
     const uint2 *ranges;
     const int *status;
+    unsigned int *work;    // persistent-kernel work counter (zeroed per render)
     TileArgs tiles;
     ParamArgs prm;
-    int width, height;
-    float *image;               // H x W x 3
-    float *saved;               // (7 + K) planes of H*W, or nullptr
     unsigned long long *stats;
 };
 
@@ -92,28 +128,29 @@ struct BlendBwdArgs {
     const uint32_t *vals;
     const uint2 *ranges;
     const int *status;
+    unsigned int *work;
     TileArgs tiles;
     ParamArgs prm;
-    int width, height;
-    const float *saved;
-    const float *dl_dimg;
-    float *acc;                 // n * 16
-    int64_t n;                  // Gaussians (bounds the saved core ids)
+    float *acc;            // n_rec * 16
 };
 
-__global__ void preprocess_kernel(PreArgs a);
-__global__ void preprocess_backward_kernel(PreBwdArgs a);
+__global__ void preprocess_kernel(const __grid_constant__ Batch b, PreArgs a);
+__global__ void preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a);
 
-// Binning: scan of per-block sums, then emit (tile key, gid) instances.
+// Binning: scan of per-block sums, then emit (global tile, record) instances.
 void launch_scan_blocks(const BinArgs &a, cudaStream_t s);
-void launch_emit(const BinArgs &a, cudaStream_t s);
+void launch_emit(const Batch &b, const BinArgs &a, cudaStream_t s);
 // Stable LSD radix sort of (key, value) pairs by the low `passes * 8` bits.
 // Returns the buffer index (0 or 1) holding the result.
 int launch_sort(const SortArgs &a, cudaStream_t s);
-void launch_ranges(RangeArgs a, int n_tiles, cudaStream_t s);
+void launch_ranges(RangeArgs a, cudaStream_t s);
 
-// Blend kernels; return false when (K, tile shape, px/thread) has no instance.
-bool launch_blend_fwd(const BlendFwdArgs &a, int px_per_thread, cudaStream_t s);
-bool launch_blend_bwd(const BlendBwdArgs &a, int px_per_thread, cudaStream_t s);
+// Persistent blend kernels over the batch's (view, tile) items; return false
+// when (K, tile shape, px/thread) has no compiled instance.
+bool launch_blend_fwd(const Batch &b, const BlendFwdArgs &a, int px_per_thread, cudaStream_t s);
+bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s);
+
+// CTAs per SM the persistent kernels are launched with (occupancy query).
+int persistent_grid(const void *kernel, int threads, size_t dyn_smem, int items);
 
 } // namespace htgs

@@ -193,13 +193,17 @@ __device__ __forceinline__ void make_expansion(const Setup &S, const CamArgs &ca
 // K1: forward setup.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads)
-preprocess_kernel(PreArgs a) {
+preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     uint32_t count = 0;
     unsigned long long box_pixels = 0;
-    if (i < a.n) {
+    if (i < b.n_rec) {
+        // Record i is Gaussian g of the scene that view v renders.
+        const ViewDesc &V = b.v[view_of_record(b, i)];
+        const int64_t g = i - V.rec_off;
+        const CamArgs &cam = V.cam;
         Setup S;
-        setup_geometry(a.means, a.log_scales, a.quats, a.logits, i, a.cam, a.prm, S);
+        setup_geometry(V.means, V.log_scales, V.quats, V.logits, g, cam, a.prm, S);
         uint2 rect = make_uint2(1u, 0u);
         float4 rec[kRecF4];
         for (int k = 0; k < kRecF4; ++k) rec[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -214,8 +218,8 @@ preprocess_kernel(PreArgs a) {
             const float sden = rc * dot(S.A[2], S.A[2]) - S.mu[2] * S.mu[2]; // < 0
             float pc[2], hc[2];
             for (int ax = 0; ax < 2; ++ax) {
-                const float f = ax == 0 ? a.cam.fx : a.cam.fy;
-                const float c = ax == 0 ? a.cam.cx : a.cam.cy;
+                const float f = ax == 0 ? cam.fx : cam.fy;
+                const float c = ax == 0 ? cam.cx : cam.cy;
                 const V3 U = S.A[ax];
                 const float uw = S.mu[ax];
                 pc[ax] = f * (rc * dot(U, S.A[2]) - uw * S.mu[2]) / sden + c;
@@ -226,7 +230,7 @@ preprocess_kernel(PreArgs a) {
             }
             // Covered pixel rectangle, widened by a small margin against rounding
             // (a wider box only adds work; the per-pixel test decides).
-            const float lim[2] = {(float)(a.cam.width - 1), (float)(a.cam.height - 1)};
+            const float lim[2] = {(float)(cam.width - 1), (float)(cam.height - 1)};
             float lo[2], hi[2], box[4];
             bool ok = true;
             for (int ax = 0; ax < 2; ++ax) {
@@ -246,7 +250,7 @@ preprocess_kernel(PreArgs a) {
                 // Record: quadratic coefficients about the box centre.
                 const float xc = pc[0], yc = pc[1];
                 Expansion E;
-                make_expansion(S, a.cam, xc, yc, E);
+                make_expansion(S, cam, xc, yc, E);
                 float n[6], d[6], zq[6];
                 n[0] = dot(E.M0, E.M0); n[1] = 2.f * dot(E.M0, E.Mx); n[2] = 2.f * dot(E.M0, E.My);
                 n[3] = dot(E.Mx, E.Mx); n[4] = 2.f * dot(E.Mx, E.My); n[5] = dot(E.My, E.My);
@@ -269,10 +273,10 @@ preprocess_kernel(PreArgs a) {
                 float q[6];
                 for (int k = 0; k < 6; ++k) q[k] = hl * (rc * d[k] - n[k]);
                 // Colour (Sec. 3.1, identical to 3DGS): max(0, 0.5 + sum Y_k sh_k).
-                const int nc = (a.sh_degree + 1) * (a.sh_degree + 1);
+                const int nc = (V.sh_degree + 1) * (V.sh_degree + 1);
                 float Y[16];
-                sh_eval(S.dir[0], S.dir[1], S.dir[2], a.sh_degree, Y);
-                const float *sh = a.sh + i * nc * 3;
+                sh_eval(S.dir[0], S.dir[1], S.dir[2], V.sh_degree, Y);
+                const float *sh = V.sh + g * nc * 3;
                 float rgb[3] = {0.5f, 0.5f, 0.5f};
                 for (int k = 0; k < nc; ++k) {
                     rgb[0] += Y[k] * sh[3 * k + 0];
@@ -332,21 +336,40 @@ preprocess_kernel(PreArgs a) {
 // rho^2 = N / D); alpha = o e^{-N/(2D)}, so dL/do = sum(dL/dalpha alpha)/o.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads)
-preprocess_backward_kernel(PreBwdArgs a) {
+preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
-    if (i >= a.n) return;
-    const int nc = (a.sh_degree + 1) * (a.sh_degree + 1);
-    float *gmu = a.g_means + 3 * i, *gls = a.g_log_scales + 3 * i, *gq = a.g_quats + 4 * i;
-    float *gsh = a.g_sh + i * nc * 3;
+    if (i >= b.n_rec) return;
+    // Record i is Gaussian g of the scene that view v renders.
+    const ViewDesc &V = b.v[view_of_record(b, i)];
+    const int64_t g = i - V.rec_off;
+    const CamArgs &cam = V.cam;
+    const int nc = (V.sh_degree + 1) * (V.sh_degree + 1);
+    float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    float gsh[48];
+    for (int k = 0; k < nc * 3; ++k) gsh[k] = 0.f;
+    // Several views of one scene add their gradients; a scene of its own
+    // view is written (which also zeroes Gaussians outside the view).
+    auto emit = [&]() {
+        float *pm = V.g_means + 3 * g, *pl = V.g_log_scales + 3 * g, *pq = V.g_quats + 4 * g;
+        float *ps = V.g_sh + g * nc * 3;
+        if (a.accumulate) {
+            for (int k = 0; k < 3; ++k) { atomicAdd(pm + k, gmu[k]); atomicAdd(pl + k, gls[k]); }
+            for (int k = 0; k < 4; ++k) atomicAdd(pq + k, gq[k]);
+            atomicAdd(V.g_logits + g, glogit);
+            for (int k = 0; k < nc * 3; ++k) atomicAdd(ps + k, gsh[k]);
+        } else {
+            for (int k = 0; k < 3; ++k) { pm[k] = gmu[k]; pl[k] = gls[k]; }
+            for (int k = 0; k < 4; ++k) pq[k] = gq[k];
+            V.g_logits[g] = glogit;
+            for (int k = 0; k < nc * 3; ++k) ps[k] = gsh[k];
+        }
+    };
     Setup S;
-    setup_geometry(a.means, a.log_scales, a.quats, a.logits, i, a.cam, a.prm, S);
+    setup_geometry(V.means, V.log_scales, V.quats, V.logits, g, cam, a.prm, S);
     const uint2 rect = a.rect[i];
     const bool active = S.valid && ((rect.x & 0xffffu) <= (rect.x >> 16));
     if (!active) {
-        for (int k = 0; k < 3; ++k) { gmu[k] = 0.f; gls[k] = 0.f; }
-        for (int k = 0; k < 4; ++k) gq[k] = 0.f;
-        a.g_logits[i] = 0.f;
-        for (int k = 0; k < nc * 3; ++k) gsh[k] = 0.f;
+        if (!a.accumulate) emit();
         return;
     }
     const float4 *acc4 = reinterpret_cast<const float4 *>(a.acc + 16 * i);
@@ -359,7 +382,7 @@ preprocess_backward_kernel(PreBwdArgs a) {
 
     const float4 r0 = a.rec[i * kRecF4 + 4]; // (z4, z5, xc, yc)
     Expansion E;
-    make_expansion(S, a.cam, r0.z, r0.w, E);
+    make_expansion(S, cam, r0.z, r0.w, E);
     // N = n0 + n1 x' + ..., n0 = M0.M0, n1 = 2 M0.Mx, n2 = 2 M0.My, n3 = Mx.Mx,
     // n4 = 2 Mx.My, n5 = My.My; the same for D with the d vectors.
     const V3 dM0 = 2.f * (gN[0] * E.M0 + gN[1] * E.Mx + gN[2] * E.My);
@@ -381,16 +404,16 @@ preprocess_backward_kernel(PreBwdArgs a) {
     db = db + cross(E.r, dDx); dr = dr + cross(dDx, E.b);
     dr = dr + cross(E.a, dDy); da = da + cross(dDy, E.r);
     // a = fx (MT)_1 + (cx - xc)(MT)_3, b = fy (MT)_2 + (cy - yc)(MT)_3, r = (MT)_3.
-    const float ox = a.cam.cx - r0.z, oy = a.cam.cy - r0.w;
+    const float ox = cam.cx - r0.z, oy = cam.cy - r0.w;
     V3 dA[3];
     float dmuv[3];
-    dA[0] = a.cam.fx * da;           dmuv[0] = a.cam.fx * daw;
-    dA[1] = a.cam.fy * db;           dmuv[1] = a.cam.fy * dbw;
+    dA[0] = cam.fx * da;             dmuv[0] = cam.fx * daw;
+    dA[1] = cam.fy * db;             dmuv[1] = cam.fy * dbw;
     dA[2] = ox * da + oy * db + dr;  dmuv[2] = ox * daw + oy * dbw + drw;
     // A = M_rot B with B = R diag(s); mu_view = M_rot mu + t.
     float dB[3][3];
     for (int k = 0; k < 3; ++k) {
-        const float c0 = a.cam.M[0 + k], c1 = a.cam.M[4 + k], c2 = a.cam.M[8 + k];
+        const float c0 = cam.M[0 + k], c1 = cam.M[4 + k], c2 = cam.M[8 + k];
         dB[k][0] = c0 * dA[0].x + c1 * dA[1].x + c2 * dA[2].x;
         dB[k][1] = c0 * dA[0].y + c1 * dA[1].y + c2 * dA[2].y;
         dB[k][2] = c0 * dA[0].z + c1 * dA[1].z + c2 * dA[2].z;
@@ -418,11 +441,11 @@ preprocess_backward_kernel(PreBwdArgs a) {
     const float iq = 1.f / S.qnorm;
     for (int k = 0; k < 4; ++k) gq[k] = (dq[k] - S.q[k] * pdot) * iq;
     // o = sigmoid(l): dL/dl = (sum dL/dalpha alpha / o) o (1 - o).
-    a.g_logits[i] = g_aa * (1.f - S.o);
+    glogit = g_aa * (1.f - S.o);
     // Colour: channels clamped at zero pass no gradient.
     float Y[16];
-    sh_eval(S.dir[0], S.dir[1], S.dir[2], a.sh_degree, Y);
-    const float *sh = a.sh + i * nc * 3;
+    sh_eval(S.dir[0], S.dir[1], S.dir[2], V.sh_degree, Y);
+    const float *sh = V.sh + g * nc * 3;
     float raw[3] = {0.5f, 0.5f, 0.5f};
     for (int k = 0; k < nc; ++k)
         for (int ch = 0; ch < 3; ++ch) raw[ch] += Y[k] * sh[3 * k + ch];
@@ -435,12 +458,13 @@ preprocess_backward_kernel(PreBwdArgs a) {
         wdir[k] = gce[0] * sh[3 * k] + gce[1] * sh[3 * k + 1] + gce[2] * sh[3 * k + 2];
     }
     float gd[3];
-    sh_grad(S.dir[0], S.dir[1], S.dir[2], a.sh_degree, wdir, gd);
+    sh_grad(S.dir[0], S.dir[1], S.dir[2], V.sh_degree, wdir, gd);
     if (S.dist > 0.f) {
         const float pd = gd[0] * S.dir[0] + gd[1] * S.dir[1] + gd[2] * S.dir[2];
         const float id = 1.f / S.dist;
         for (int k = 0; k < 3; ++k) gmu[k] += (gd[k] - S.dir[k] * pd) * id;
     }
+    emit();
 }
 
 } // namespace htgs

@@ -133,3 +133,78 @@ def render(g: GaussianTensors, renderer: Renderer):
     """Differentiable render of one view (hybrid transparency, Eq. (15))."""
     return RenderFunction.apply(renderer, g.sh_degree, g.means, g.log_scales, g.quats,
                                 g.opacity_logits, g.sh)
+
+
+class BatchRenderer:
+    """Buffers of one batch of views (htgs_render_batch): the workspace and,
+    per view, the image and the saved state. Views that share a scene pass
+    the same GaussianTensors object; their gradients are summed."""
+
+    def __init__(self, scenes, cameras, params, launch=None, capacity=None, device="cuda", save=True):
+        assert len(scenes) == len(cameras) and 1 <= len(cameras) <= B.HTGS_MAX_VIEWS
+        self.scenes = list(scenes)
+        self.cameras = list(cameras)
+        self.params = params
+        self.launch = launch if launch is not None else B.c_launch()
+        self.device = torch.device(device)
+        self.save = save
+        n_rec = sum(s.n for s in self.scenes)
+        self.capacity = int(capacity) if capacity else max(8 * n_rec, 1 << 16)
+        self.images = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=self.device)
+                       for c in self.cameras]
+        K = int(params.K)
+        self.saved = [torch.empty(((7 + K) * c.width * c.height,), dtype=torch.float32, device=self.device)
+                      for c in self.cameras] if save else None
+        self._structs = {}
+        self._alloc()
+
+    def _struct(self, g):
+        key = id(g)
+        if key not in self._structs:
+            self._structs[key] = g.c_struct()
+        return self._structs[key]
+
+    def views(self, dl_dimages=None, grads=None):
+        gs = [self._struct(s) for s in self.scenes]
+        cg = None
+        if grads is not None:
+            cg = [B.GaussiansGrad(*[B._ptr(grads[id(s)][f]).value for f in FIELDS]) for s in self.scenes]
+        return B.c_views(gs, self.cameras, self.images, self.saved, dl_dimages, cg)
+
+    def _alloc(self):
+        nbytes = B.htgs_batch_workspace_size(self.views(), self.params, self.launch, self.capacity)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+
+    def forward(self, check=True, stream=None, views=None):
+        views = views if views is not None else self.views()
+        for _ in range(4):
+            B._check(B.htgs_render_batch(views, self.params, self.launch, self.workspace, self.capacity, stream),
+                     "htgs_render_batch")
+            if not check:
+                return self.images
+            st, inst = B.htgs_get_error(self.workspace, stream)
+            if st == B.HTGS_ERR_OVERFLOW:
+                self.capacity = max(int(inst * 1.25) + 1024, self.capacity)
+                self._alloc()
+                continue
+            B._check(st, "htgs_render_batch (device)")
+            self.last_instances = inst
+            return self.images
+        raise B.HTGSError(B.HTGS_ERR_OVERFLOW, "htgs_render_batch")
+
+    def gradient_buffers(self):
+        """One set of gradient tensors per distinct scene (keyed by id)."""
+        out = {}
+        for s in self.scenes:
+            if id(s) not in out:
+                out[id(s)] = {f: torch.empty_like(getattr(s, f)) for f in FIELDS}
+        return out
+
+    def backward(self, dl_dimages, grads=None, stream=None):
+        if grads is None:
+            grads = self.gradient_buffers()
+        dls = [d.contiguous() for d in dl_dimages]
+        views = self.views(dl_dimages=dls, grads=grads)
+        B._check(B.htgs_render_batch_backward(views, self.params, self.launch, self.workspace, self.capacity,
+                                              stream), "htgs_render_batch_backward")
+        return grads

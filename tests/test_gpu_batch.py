@@ -1,0 +1,125 @@
+"""The batched form: many views of uneven resolution, of one scene or of
+several scenes of uneven size, in one launch per phase (persistent blend over
+a (view, tile) queue), capturable in a CUDA graph. Each view's result must
+equal rendering it alone, and the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_08129_gb300 import binding as B
+from paper_2410_08129_gb300 import scenes
+from paper_2410_08129_gb300.renderer import FIELDS, BatchRenderer, GaussianTensors, Renderer
+from tests.gpu_util import IMAGE_TOL, MAX_AMBIGUOUS, compare_images
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(80, 60), (123, 77), (64, 64), (200, 150), (33, 47)]
+
+
+def _cameras(sizes, seed=0):
+    rng = np.random.default_rng(seed)
+    cams = []
+    for w, h in sizes:
+        d = rng.standard_normal(3)
+        d[2] = -abs(d[2]) - 1.0
+        d /= np.linalg.norm(d)
+        eye = np.array([0.0, 0.0, 3.0]) + 4.5 * d
+        cams.append(scenes.fov_camera(scenes.look_at(eye, (0.0, 0.0, 3.0)), w, h, 60.0).rounded())
+    return cams
+
+
+def _scene(n, seed, degree=1):
+    s = scenes.small_box_scene(n, seed=seed, sh_degree=degree)
+    s.log_scales -= np.float32(0.5)
+    return s
+
+
+def test_batch_of_views_equals_single_renders():
+    scene = _scene(3000, 1)
+    g = GaussianTensors.from_scene(scene)
+    cams = _cameras(SIZES)
+    prm = scenes.Params(K=8, bg=(0.1, 0.2, 0.3))
+    br = BatchRenderer([g] * len(cams), cams, prm)
+    imgs = [im.clone() for im in br.forward()]
+    for cam, img in zip(cams, imgs):
+        ref = Renderer(cam, prm, scene.n).forward(g)
+        assert float((img - ref).abs().max()) <= 1e-6
+
+
+def test_batch_of_scenes_equals_single_renders():
+    sc = [_scene(n, 10 + i, degree=i % 4) for i, n in enumerate([100, 1000, 5000])]
+    gs = [GaussianTensors.from_scene(s) for s in sc]
+    cams = _cameras(SIZES[:3], seed=1)
+    prm = scenes.Params(K=4)
+    br = BatchRenderer(gs, cams, prm, launch=B.c_launch((16, 8), 2))
+    imgs = [im.clone() for im in br.forward()]
+    for g, cam, img in zip(gs, cams, imgs):
+        ref = Renderer(cam, prm, g.n, launch=B.c_launch((16, 8), 2)).forward(g)
+        assert float((img - ref).abs().max()) <= 1e-6
+
+
+def test_batch_view_matches_oracle():
+    scene = _scene(1500, 2, degree=2)
+    g = GaussianTensors.from_scene(scene)
+    cams = _cameras(SIZES[:4], seed=2)
+    prm = scenes.Params(K=8, bg=(0.3, 0.3, 0.3))
+    imgs = BatchRenderer([g] * len(cams), cams, prm).forward()
+    for cam, img in zip(cams, imgs):
+        ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+        e_ok, amb, _ = compare_images(img.cpu().numpy().astype(np.float64), ref, d["ambiguous"])
+        assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS, (cam.width, cam.height, e_ok, amb)
+
+
+def test_batch_backward_sums_views_of_one_scene():
+    scene = _scene(2000, 3, degree=1)
+    g = GaussianTensors.from_scene(scene)
+    other = GaussianTensors.from_scene(_scene(700, 4, degree=1))
+    cams = _cameras(SIZES[:4], seed=3)
+    prm = scenes.Params(K=8)
+    views = [g, g, other, g]
+    br = BatchRenderer(views, cams, prm)
+    br.forward()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    dls = [torch.randn(im.shape, device="cuda", generator=gen) for im in br.images]
+    grads = br.backward(dls)
+    torch.cuda.synchronize()
+    want = {f: torch.zeros_like(getattr(g, f)) for f in FIELDS}
+    for cam, dl, s in zip(cams, dls, views):
+        r = Renderer(cam, prm, s.n)
+        r.forward(s)
+        single = r.backward(s, dl)
+        if s is g:
+            for f in FIELDS:
+                want[f] += single[f]
+        else:
+            for f in FIELDS:
+                torch.testing.assert_close(grads[id(other)][f], single[f], rtol=1e-6, atol=1e-9)
+    for f in FIELDS:
+        torch.testing.assert_close(grads[id(g)][f], want[f], rtol=1e-4, atol=1e-6 * float(want[f].abs().max()))
+
+
+def test_batch_captured_in_cuda_graph():
+    scene = _scene(2000, 5)
+    g = GaussianTensors.from_scene(scene)
+    cams = _cameras(SIZES, seed=4)
+    prm = scenes.Params(K=8)
+    br = BatchRenderer([g] * len(cams), cams, prm)
+    eager = [im.clone() for im in br.forward(check=True)]
+    views = br.views()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        br.forward(check=False, views=views)   # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    for im in br.images:
+        im.zero_()
+    with torch.cuda.graph(graph, stream=stream):
+        br.forward(check=False, views=views)
+    graph.replay()
+    torch.cuda.synchronize()
+    st, _ = B.htgs_get_error(br.workspace)
+    assert st == B.HTGS_OK
+    for a, b in zip(eager, br.images):
+        assert torch.equal(a, b)
