@@ -93,8 +93,10 @@ def test_batch_backward_sums_views_of_one_scene():
             for f in FIELDS:
                 want[f] += single[f]
         else:
+            # Accumulators are atomic float sums over tiles: equal up to summation order.
             for f in FIELDS:
-                torch.testing.assert_close(grads[id(other)][f], single[f], rtol=1e-6, atol=1e-9)
+                torch.testing.assert_close(grads[id(other)][f], single[f], rtol=1e-5,
+                                           atol=1e-6 * float(single[f].abs().max()))
     for f in FIELDS:
         torch.testing.assert_close(grads[id(g)][f], want[f], rtol=1e-4, atol=1e-6 * float(want[f].abs().max()))
 
