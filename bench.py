@@ -141,6 +141,220 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _chunks(instances, limit):
+    """Consecutive groups of views whose instance sums stay under `limit`."""
+    out, cur, tot = [], [], 0
+    for i, n in enumerate(instances):
+        if cur and tot + n > limit:
+            out.append(cur)
+            cur, tot = [], 0
+        cur.append(i)
+        tot += n
+    if cur:
+        out.append(cur)
+    return out
+
+
+def plain_vs_batched(gs, tgs, cams, prm, steps, warmup, tune_views=None, graph=True):
+    """One training-style step over a set of views, (a) as the plain per-view
+    loop (htgs_render, htgs_l1_loss_grad, htgs_render_backward per view,
+    gradients of a shared scene summed) and (b) as the batched form
+    (htgs_render_batch + per-view loss + htgs_render_batch_backward, captured
+    in a CUDA graph), both with the launch configuration the autotuner picks.
+    Returns frames/s of the forward alone and steps/s of the whole step."""
+    import torch
+    from paper_2410_08129_gb300 import binding as B
+    from paper_2410_08129_gb300.autotune import autotune
+    from paper_2410_08129_gb300.renderer import FIELDS, BatchRenderer, Renderer
+
+    n_views = len(cams)
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev).manual_seed(7)
+
+    # -- autotune (tile shape, forward pixels per thread) on fwd+bwd of a subset
+    sub = tune_views if tune_views is not None else list(range(n_views))
+
+    def step_for_launch(launch):
+        br = BatchRenderer([gs[i] for i in sub], [cams[i] for i in sub], prm, launch=launch)
+        br.forward(check=True)
+        dls = [torch.randn(im.shape, device=dev, generator=gen) * 1e-3 for im in br.images]
+        grads = br.gradient_buffers()
+
+        def step():
+            br.forward(check=False)
+            br.backward(dls, grads=grads)
+        return step
+
+    t0 = time.perf_counter()
+    launch, tune_ms = autotune(step_for_launch, warmup=1, repeats=2)
+    tune_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    tile, ppt = (launch.tile_w, launch.tile_h), launch.px_per_thread
+
+    # -- plain: one Renderer per view ------------------------------------------
+    rs = [Renderer(c, prm, g.n, launch=launch) for g, c in zip(gs, cams)]
+    imgs = [r.image_buffer() for r in rs]
+    targets = [r.forward(t, save=False, check=True).clone() for r, t in zip(rs, tgs)]
+    for r, g, im in zip(rs, gs, imgs):
+        r.forward(g, image=im, save=True, check=True)
+    inst = [int(r.last_instances) for r in rs]
+    dls = [torch.empty_like(im) for im in imgs]
+    losses = torch.zeros(n_views, dtype=torch.float32, device=dev)
+    distinct = {}
+    for g in gs:
+        distinct.setdefault(id(g), g)
+    acc = {k: {f: torch.zeros_like(getattr(g, f)) for f in FIELDS} for k, g in distinct.items()}
+    tmp = {k: {f: torch.empty_like(getattr(g, f)) for f in FIELDS} for k, g in distinct.items()}
+
+    def plain_fwd():
+        for r, g, im in zip(rs, gs, imgs):
+            r.forward(g, image=im, save=False, check=False)
+
+    def plain_step():
+        seen = set()
+        for i, (r, g, im) in enumerate(zip(rs, gs, imgs)):
+            r.forward(g, image=im, save=True, check=False)
+            B._check(B.htgs_l1_loss_grad(im, targets[i], dls[i], losses[i:i + 1]), "l1")
+            if id(g) not in seen:
+                r.backward(g, dls[i], grads=acc[id(g)])
+                seen.add(id(g))
+            else:
+                r.backward(g, dls[i], grads=tmp[id(g)])
+                for f in FIELDS:
+                    acc[id(g)][f].add_(tmp[id(g)][f])
+
+    # -- batched: as few batches as the instance limit allows -------------------
+    groups = _chunks(inst, int(0.97 * B.HTGS_MAX_CAPACITY))
+    brs, bviews_f, bviews_b, bgrads, bdls, blosses = [], [], [], [], [], []
+    for grp in groups:
+        br = BatchRenderer([gs[i] for i in grp], [cams[i] for i in grp], prm, launch=launch,
+                           capacity=min(int(sum(inst[i] for i in grp) * 1.02) + 4096, B.HTGS_MAX_CAPACITY))
+        br.forward(check=True)
+        gr = br.gradient_buffers()
+        dl = [torch.empty_like(im) for im in br.images]
+        brs.append(br)
+        bdls.append(dl)
+        bgrads.append(gr)
+        blosses.append(torch.zeros(len(grp), dtype=torch.float32, device=dev))
+        bviews_f.append(br.views())
+        bviews_b.append(br.views(dl_dimages=dl, grads=gr))
+    bacc = {k: {f: torch.zeros_like(getattr(g, f)) for f in FIELDS} for k, g in distinct.items()} \
+        if len(groups) > 1 else bgrads[0]
+
+    def batched_fwd():
+        for br, v in zip(brs, bviews_f):
+            B._check(B.htgs_render_batch(v, prm, launch, br.workspace, br.capacity), "htgs_render_batch")
+
+    def batched_step():
+        for j, (br, grp) in enumerate(zip(brs, groups)):
+            B._check(B.htgs_render_batch(bviews_f[j], prm, launch, br.workspace, br.capacity), "htgs_render_batch")
+            for k, i in enumerate(grp):
+                B._check(B.htgs_l1_loss_grad(br.images[k], targets[i], bdls[j][k], blosses[j][k:k + 1]), "l1")
+            B._check(B.htgs_render_batch_backward(bviews_b[j], prm, launch, br.workspace, br.capacity),
+                     "htgs_render_batch_backward")
+            if len(groups) > 1:
+                for key, gd in bgrads[j].items():
+                    for f in FIELDS:
+                        bacc[key][f].add_(gd[f]) if j else bacc[key][f].copy_(gd[f])
+
+    graphs = {}
+    if graph:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            batched_fwd()
+            batched_step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        for name, fn in (("fwd", batched_fwd), ("step", batched_step)):
+            gph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gph, stream=side):
+                fn()
+            graphs[name] = gph
+    run_bfwd = graphs["fwd"].replay if graph else batched_fwd
+    run_bstep = graphs["step"].replay if graph else batched_step
+
+    def timed(fn, k):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms = {"plain_fwd": timed(plain_fwd, steps), "batched_fwd": timed(run_bfwd, steps),
+          "plain_step": timed(plain_step, steps), "batched_step": timed(run_bstep, steps)}
+    for r in rs:
+        st, _ = r.status()
+        assert st == B.HTGS_OK, B.htgs_status_string(st)
+    for br in brs:
+        st, _ = B.htgs_get_error(br.workspace)
+        assert st == B.HTGS_OK, B.htgs_status_string(st)
+
+    # Same images and (up to atomic summation order) the same gradients.
+    plain_step()
+    run_bstep()
+    torch.cuda.synchronize()
+    img_diff = 0.0
+    for j, grp in enumerate(groups):
+        for k, i in enumerate(grp):
+            img_diff = max(img_diff, float((brs[j].images[k] - imgs[i]).abs().max()))
+    grad_rel = 0.0
+    for key in distinct:
+        for f in FIELDS:
+            a, b = acc[key][f], bacc[key][f]
+            grad_rel = max(grad_rel, float((a - b).abs().max() / a.abs().max().clamp_min(1e-30)))
+    return {
+        "views": n_views, "gaussians": [int(g.n) for g in distinct.values()],
+        "pixels": int(sum(c.width * c.height for c in cams)), "instances": int(sum(inst)),
+        "launch": {"tile": f"{tile[0]}x{tile[1]}", "px_per_thread": int(ppt),
+                   "autotune_ms_per_step": {f"{t[0]}x{t[1]}/ppt{p}": round(v, 3) for (t, p), v in tune_ms.items()},
+                   "autotune_views": len(sub), "autotune_s": round(tune_s, 1)},
+        "batches": len(groups), "cuda_graph": bool(graph),
+        "fwd": {"plain_frames_per_s": n_views * 1e3 / ms["plain_fwd"],
+                "batched_frames_per_s": n_views * 1e3 / ms["batched_fwd"],
+                "speedup": ms["plain_fwd"] / ms["batched_fwd"]},
+        "fwd_bwd": {"plain_steps_per_s": 1e3 / ms["plain_step"], "batched_steps_per_s": 1e3 / ms["batched_step"],
+                    "speedup": ms["plain_step"] / ms["batched_step"]},
+        "ms": {k: round(v, 3) for k, v in ms.items()},
+        "max_abs_image_diff": img_diff, "max_rel_grad_diff": grad_rel,
+    }
+
+
+def batched_leg(steps, warmup):
+    """Config-4 workloads: 32 views (320x240 .. 1600x1064) of a 3M-Gaussian
+    scene, and 8 scenes of 50k .. 2M Gaussians at 1280x720; K = 8."""
+    import torch
+    from paper_2410_08129_gb300 import scenes
+    from paper_2410_08129_gb300.renderer import GaussianTensors
+    prm = scenes.Params(K=8)
+    rng = np.random.Generator(np.random.PCG64(44))
+    scene = scenes.config4_scene()
+    g = GaussianTensors.from_scene(scene)
+    tg = GaussianTensors.from_scene(scenes.perturbed(scene, rng))
+    del scene
+    cams = [c.rounded() for c in scenes.config4_views()]
+    out = {"views32": plain_vs_batched([g] * len(cams), [tg] * len(cams), cams, prm, steps, warmup,
+                                       tune_views=list(range(0, len(cams), 8)))}
+    out["views32"]["workload"] = ("32 views of one 3M-Gaussian scene (config-1 distribution), "
+                                  "320x240..1600x1064, cameras on a 6 m sphere, K=8")
+    del g, tg
+    torch.cuda.empty_cache()
+    multi = scenes.config4_multi()
+    gs = [GaussianTensors.from_scene(s) for s, _ in multi]
+    tgs = [GaussianTensors.from_scene(scenes.perturbed(s, rng)) for s, _ in multi]
+    cams = [c.rounded() for _, c in multi]
+    del multi
+    out["scenes8"] = plain_vs_batched(gs, tgs, cams, prm, steps, warmup)
+    out["scenes8"]["workload"] = "8 scenes of 50k..2M Gaussians (config-1 distribution), 1280x720 each, K=8"
+    torch.cuda.empty_cache()
+    return out
+
+
 def profile_case(which: str, warmup: int):
     """A few untimed steps of the headline render (fwd) or of the training
     step (train): `warmup` steps, then 2 more, nothing else on the GPU."""
@@ -182,6 +396,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the plain-vs-batched comparison")
+    ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--batched-warmup", type=int, default=3)
     ap.add_argument("--profile", choices=["fwd", "train"], default=None,
                     help="run a few untimed steps of one workload (for an external profiler) and exit")
     args = ap.parse_args()
@@ -347,6 +564,13 @@ def main():
         except (OSError, ValueError):
             traffic = None
 
+    batched = None
+    if not args.no_batched:
+        del r, tr, g, tg, tt, grads, image, timg, dl, target
+        torch.cuda.empty_cache()
+        barrier()
+        batched = batched_leg(args.batched_steps, args.batched_warmup)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, cam, prm)
@@ -365,6 +589,7 @@ def main():
                     "workload": "500k Gaussians (box distribution), 1200x800, K=8: render + L1 + backward",
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
                     "grads_finite": gfinite},
+        "batched_vs_plain": batched,
         "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": traffic,

@@ -43,6 +43,8 @@ typedef int32_t htgs_status;
 
 /* Largest core size K compiled into the blend kernels. */
 #define HTGS_MAX_K 32
+/* Largest instance_capacity: instance indices are 32-bit. */
+#define HTGS_MAX_CAPACITY 2147483647ll
 
 /* Scene parameters (Sec. 3.1). N Gaussians; n_coeff = (sh_degree + 1)^2.
  *   means          N x 3        world-space mean mu
@@ -105,7 +107,7 @@ typedef struct {
 } htgs_launch;
 
 /* Sizes of the caller-owned buffers for one camera.
- *   instance_capacity  maximum number of (Gaussian, tile) instances
+ *   instance_capacity  maximum number of (Gaussian, tile) instances, 0 .. HTGS_MAX_CAPACITY
  *   fwd_bytes    [out] workspace bytes needed by htgs_render / htgs_render_backward
  *   saved_bytes  [out] per-pixel state htgs_render saves for the backward:
  *                (7 + K) * width * height * 4 bytes
@@ -123,10 +125,22 @@ htgs_status htgs_workspace_size(int64_t n_gaussians, const htgs_camera *cam,
  *   sorted_vals  capacity x uint32: the matching Gaussian ids
  *   ranges       n_tiles x uint2: [start, end) of each tile in the sorted list
  *   acc          n x 16 float: gradient accumulators of the blend adjoint
+ *   items        max_items x int4: blend work items (tile, chunk k, chunks m,
+ *                first partial-state slot), longest chunks first
+ *   n_items      1 x uint32: number of items of the last render
+ *   partials     slots x (6 + 2K) x tile pixels float: partial states of split
+ *                tiles (sum alpha, sum alpha rgb, prod (1 - alpha), count as
+ *                int bits, then K (depth, gid bits) pairs), pixel-minor
+ * A tile whose list is longer than max(1024, instances / 2048) is cut into
+ * m > 1 chunks processed by different CTAs (at most slots chunks in all);
+ * the forward merges their partial states, so the result does not depend
+ * on the cut except for the order of floating-point sums.
  * Same argument rules as htgs_workspace_size; out is a host pointer. */
 typedef struct {
     uint64_t rec, rect, count, sorted_keys, sorted_vals, ranges, acc;
     int32_t n_tiles, tiles_x, tiles_y, tile_bits;
+    uint64_t items, n_items, partials;
+    int32_t max_items, slots;
 } htgs_layout;
 
 htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam,
@@ -196,6 +210,14 @@ typedef struct {
 htgs_status htgs_batch_workspace_size(int32_t n_views, const htgs_view *views,
                                       const htgs_params *params, const htgs_launch *launch,
                                       int64_t instance_capacity, size_t *workspace_bytes);
+
+/* Offsets of the internal buffers of a batch workspace (see htgs_layout):
+ * records of view v start at record sum_{u < v} n_u, tiles of view v at
+ * tile sum_{u < v} tiles_x(u) * tiles_y(u); tiles_x and tiles_y describe
+ * view 0. Host pointers; nothing is read on the device. */
+htgs_status htgs_batch_workspace_layout(int32_t n_views, const htgs_view *views,
+                                        const htgs_params *params, const htgs_launch *launch,
+                                        int64_t instance_capacity, htgs_layout *out);
 
 /* Forward render of every view of a batch (Eq. (15) per pixel of each view).
  * Errors and overflow as for htgs_render (htgs_get_error on the workspace). */

@@ -25,6 +25,7 @@ HTGS_ERR_CUDA = 4
 HTGS_ERR_TIMEOUT = 5
 HTGS_ERR_NOT_SUPPORTED = 6
 HTGS_MAX_K = 32
+HTGS_MAX_CAPACITY = (1 << 31) - 1
 
 
 class Gaussians(ctypes.Structure):
@@ -60,7 +61,10 @@ class Layout(ctypes.Structure):
     _fields_ = [("rec", ctypes.c_uint64), ("rect", ctypes.c_uint64), ("count", ctypes.c_uint64),
                 ("sorted_keys", ctypes.c_uint64), ("sorted_vals", ctypes.c_uint64),
                 ("ranges", ctypes.c_uint64), ("acc", ctypes.c_uint64), ("n_tiles", ctypes.c_int32),
-                ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("tile_bits", ctypes.c_int32)]
+                ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
+                ("items", ctypes.c_uint64), ("n_items", ctypes.c_uint64), ("partials", ctypes.c_uint64),
+                ("max_items", ctypes.c_int32),
+                ("slots", ctypes.c_int32)]
 
 
 _lib = None
@@ -280,12 +284,24 @@ def _batch_lib():
         L.htgs_batch_workspace_size.argtypes = [ctypes.c_int32, P(View), P(Params), P(Launch), ctypes.c_int64,
                                                 P(ctypes.c_size_t)]
         L.htgs_batch_workspace_size.restype = ctypes.c_int32
+        L.htgs_batch_workspace_layout.argtypes = [ctypes.c_int32, P(View), P(Params), P(Launch), ctypes.c_int64,
+                                                  P(Layout)]
+        L.htgs_batch_workspace_layout.restype = ctypes.c_int32
         for f in ("htgs_render_batch", "htgs_render_batch_backward"):
             getattr(L, f).argtypes = [ctypes.c_int32, P(View), P(Params), P(Launch), ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_int64, ctypes.c_void_p]
             getattr(L, f).restype = ctypes.c_int32
         L._batch_ready = True
     return L
+
+
+def htgs_batch_workspace_layout(views, params, launch, capacity) -> Layout:
+    out = Layout()
+    st = _batch_lib().htgs_batch_workspace_layout(len(views), views, ctypes.byref(c_params(params)),
+                                                  ctypes.byref(launch) if launch is not None else None,
+                                                  int(capacity), ctypes.byref(out))
+    _check(st, "htgs_batch_workspace_layout")
+    return out
 
 
 def htgs_batch_workspace_size(views, params, launch, capacity):

@@ -7,6 +7,7 @@
 // workspace region, preprocess, scan, emit, histogram + onesweep passes,
 // ranges, persistent blend. Nothing synchronises the stream, so the whole
 // sequence can be captured in a CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -18,16 +19,16 @@ namespace htgs {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int64_t kMaxCapacity = (1ll << 30) - 1; // look-back count field
+constexpr int64_t kMaxCapacity = HTGS_MAX_CAPACITY;  // 32-bit indices, headroom for grid strides
 constexpr int64_t kMaxRecords = 0xfffffffell;     // record ids are 32-bit
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     // byte offsets inside the workspace
-    size_t status, stats, total, work, ghist, tickets, ranges, lookback, zero_end;
-    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, bwd_work, acc, end;
-    int n_blocks, n_sort_blocks, passes;
+    size_t status, stats, total, work, ghist, tickets, ranges, lookback, n_items, done, zero_end;
+    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, end;
+    int n_blocks, n_sort_blocks, passes, slots_cap, max_items;
     TileArgs tiles;
     int64_t n_rec;
 };
@@ -97,7 +98,12 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     L.ghist = o; o = align_up(o + kMaxPasses * kRadix * sizeof(uint32_t));
     L.tickets = o; o = align_up(o + kMaxPasses * sizeof(uint32_t));
     L.ranges = o; o = align_up(o + (size_t)n_tiles * sizeof(uint2));
-    L.lookback = o; o = align_up(o + (size_t)L.passes * L.n_sort_blocks * kRadix * sizeof(uint32_t));
+    L.lookback = o; o = align_up(o + (size_t)L.passes * L.n_sort_blocks * kRadix * sizeof(unsigned long long));
+    // Split-tile slots: enough for chunks of kMinChunk over the whole capacity, at most kMaxSlots.
+    L.slots_cap = (int)std::min<int64_t>(kMaxSlots, 2 * ((capacity + kMinChunk - 1) / kMinChunk) + 2);
+    L.max_items = (int)(n_tiles + L.slots_cap);
+    L.n_items = o; o = align_up(o + 4 * sizeof(uint32_t));
+    L.done = o; o = align_up(o + (size_t)L.slots_cap * sizeof(uint32_t));
     L.zero_end = o;
     L.rec = o; o = align_up(o + (size_t)n_rec * kRecF4 * sizeof(float4));
     L.rect = o; o = align_up(o + (size_t)n_rec * sizeof(uint2));
@@ -107,6 +113,9 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     L.vals0 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.keys1 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.vals1 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
+    L.items = o; o = align_up(o + (size_t)L.max_items * sizeof(int4));
+    L.partials = o;
+    o = align_up(o + (size_t)L.slots_cap * (6 + 2 * prm->K) * L.tiles.tile_w * L.tiles.tile_h * sizeof(float));
     L.bwd_work = o; o = align_up(o + 4 * sizeof(uint32_t));
     L.acc = o; o = align_up(o + (size_t)n_rec * 16 * sizeof(float));
     L.end = o;
@@ -253,7 +262,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     so.keys[0] = at<uint32_t>(workspace, L.keys0); so.vals[0] = at<uint32_t>(workspace, L.vals0);
     so.keys[1] = at<uint32_t>(workspace, L.keys1); so.vals[1] = at<uint32_t>(workspace, L.vals1);
     so.ghist = at<uint32_t>(workspace, L.ghist);
-    so.lookback = at<uint32_t>(workspace, L.lookback);
+    so.lookback = at<unsigned long long>(workspace, L.lookback);
     so.tickets = at<uint32_t>(workspace, L.tickets);
     so.n_sort_blocks = L.n_sort_blocks; so.status = status;
     const int sb = launch_sort(so, s);
@@ -263,10 +272,20 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     ra.ranges = at<uint2>(workspace, L.ranges); ra.n_tiles = L.tiles.n_tiles;
     launch_ranges(ra, s);
 
+    ScheduleArgs sc{};
+    sc.total = total; sc.ranges = ra.ranges; sc.n_tiles = L.tiles.n_tiles;
+    sc.slots_cap = L.slots_cap;
+    sc.items = at<int4>(workspace, L.items);
+    sc.n_items = at<uint32_t>(workspace, L.n_items);
+    launch_schedule(sc, s);
+
     BlendFwdArgs ba{};
     ba.rec = at<float4>(workspace, L.rec);
     ba.vals = so.vals[sb];
     ba.ranges = at<uint2>(workspace, L.ranges);
+    ba.items = sc.items; ba.n_items = sc.n_items; ba.max_items = L.max_items; ba.slots = L.slots_cap;
+    ba.partials = at<float>(workspace, L.partials);
+    ba.done = at<unsigned int>(workspace, L.done);
     ba.status = status;
     ba.work = at<unsigned int>(workspace, L.work);
     ba.tiles = L.tiles; ba.prm = pa;
@@ -336,6 +355,9 @@ htgs_status render_batch_backward(int n_views, const htgs_view *views, const htg
     bb.rec = at<float4>(workspace, L.rec);
     bb.vals = at<uint32_t>(workspace, sb ? L.vals1 : L.vals0);
     bb.ranges = at<uint2>(workspace, L.ranges);
+    bb.items = at<int4>(workspace, L.items);
+    bb.n_items = at<uint32_t>(workspace, L.n_items);
+    bb.max_items = L.max_items;
     bb.status = at<int>(workspace, L.status);
     bb.work = at<unsigned int>(workspace, L.bwd_work);
     bb.tiles = L.tiles; bb.prm = pa;
@@ -414,13 +436,8 @@ htgs_status htgs_batch_workspace_size(int32_t n_views, const htgs_view *views, c
     return HTGS_OK;
 }
 
-htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam, const htgs_params *params,
-                                  const htgs_launch *launch, int64_t instance_capacity, htgs_layout *out) {
-    if (!out || !camera_ok(cam)) return HTGS_ERR_INVALID_ARG;
-    HostView hv{n_gaussians, cam};
-    Layout L;
-    htgs_status st = make_layout(1, &hv, params, launch, instance_capacity, L);
-    if (st) return st;
+namespace {
+void fill_layout(const Layout &L, const htgs_camera *cam, htgs_layout *out) {
     const int sb = sorted_buffer(L);
     out->rec = L.rec;
     out->rect = L.rect;
@@ -433,6 +450,35 @@ htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam, c
     out->tiles_x = (cam->width + L.tiles.tile_w - 1) / L.tiles.tile_w;
     out->tiles_y = (cam->height + L.tiles.tile_h - 1) / L.tiles.tile_h;
     out->tile_bits = L.tiles.tile_bits;
+    out->items = L.items;
+    out->n_items = L.n_items;
+    out->partials = L.partials;
+    out->max_items = L.max_items;
+    out->slots = L.slots_cap;
+}
+} // namespace
+
+htgs_status htgs_workspace_layout(int64_t n_gaussians, const htgs_camera *cam, const htgs_params *params,
+                                  const htgs_launch *launch, int64_t instance_capacity, htgs_layout *out) {
+    if (!out || !camera_ok(cam)) return HTGS_ERR_INVALID_ARG;
+    HostView hv{n_gaussians, cam};
+    Layout L;
+    htgs_status st = make_layout(1, &hv, params, launch, instance_capacity, L);
+    if (st) return st;
+    fill_layout(L, cam, out);
+    return HTGS_OK;
+}
+
+htgs_status htgs_batch_workspace_layout(int32_t n_views, const htgs_view *views, const htgs_params *params,
+                                        const htgs_launch *launch, int64_t instance_capacity, htgs_layout *out) {
+    if (!out) return HTGS_ERR_INVALID_ARG;
+    HostView hv[kMaxViews];
+    htgs_status st = collect(n_views, views, hv);
+    if (st) return st;
+    Layout L;
+    st = make_layout(n_views, hv, params, launch, instance_capacity, L);
+    if (st) return st;
+    fill_layout(L, &views[0].camera, out);
     return HTGS_OK;
 }
 

@@ -24,14 +24,14 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -170,9 +170,11 @@ __global__ void __launch_bounds__(kSortThreads) histogram_kernel(SortArgs a) {
 // One stable scatter pass. Blocks take tickets in launch order so that every
 // block they wait on is already resident; waits are bounded.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kCountMask = (1u << 30) - 1;
+// Look-back word: status in the top two bits, digit count below (64-bit so
+// that counts up to the 2^31 - 1 instance limit fit beside the flags).
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kCountMask = (1ull << 62) - 1;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
@@ -248,8 +250,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
             s_whist[w][d] = run;
             run += c;
         }
-        uint32_t *lb = a.lookback + ((size_t)pass * a.n_sort_blocks) * kRadix;
-        uint32_t excl = 0;
+        unsigned long long *lb = a.lookback + ((size_t)pass * a.n_sort_blocks) * kRadix;
+        unsigned long long excl = 0;
         if (t == 0) {
             st_relaxed(&lb[d], kFlagInc | run);
         } else {
@@ -257,8 +259,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
             int pred = t - 1;
             uint32_t spins = 0;
             while (pred >= 0) {
-                const uint32_t v = ld_relaxed(&lb[(size_t)pred * kRadix + d]);
-                const uint32_t flag = v & ~kCountMask;
+                const unsigned long long v = ld_relaxed(&lb[(size_t)pred * kRadix + d]);
+                const unsigned long long flag = v & ~kCountMask;
                 if (flag == 0) {
                     if (++spins > kSpinLimit) {
                         set_error(a.status, HTGS_ERR_TIMEOUT);
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
             }
             st_relaxed(&lb[(size_t)t * kRadix + d], kFlagInc | ((excl + run) & kCountMask));
         }
-        s_base[d] = s_scan[d] + excl;
+        s_base[d] = s_scan[d] + (uint32_t)excl;
     }
     __syncthreads();
 
@@ -304,7 +306,65 @@ __global__ void ranges_kernel(RangeArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Blend work items (one CTA): chunk the long tile lists, then bucket the
+// items by chunk length (two buckets per octave, longest first).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int length_bucket(uint32_t len) {
+    if (len == 0) return kSchedBuckets - 1;
+    const int l = 31 - __clz(len);
+    const int sub = l > 0 ? (int)((len >> (l - 1)) & 1u) : 0;
+    return (kSchedBuckets - 2) - min(2 * l + sub, kSchedBuckets - 2);
+}
+
+__global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a) {
+    __shared__ uint32_t s_cnt[kSchedBuckets];
+    __shared__ uint32_t s_pos[kSchedBuckets];
+    __shared__ uint32_t s_slots;
+    const int tid = threadIdx.x;
+    const uint64_t total = *a.total;
+    uint64_t chunk = (total + kChunkDiv - 1) / kChunkDiv;
+    if (chunk < kMinChunk) chunk = kMinChunk;
+    // Every split tile uses m < 2 count / chunk slots: keep the sum within the cap.
+    const uint64_t need = (2 * total + (uint64_t)a.slots_cap - 1) / (uint64_t)max(a.slots_cap, 1);
+    if (chunk < need) chunk = need;
+    auto parts = [&](uint32_t cnt) -> int {
+        return cnt > chunk ? (int)((cnt + chunk - 1) / chunk) : 1;
+    };
+    for (int b = tid; b < kSchedBuckets; b += kSchedThreads) s_cnt[b] = 0;
+    if (tid == 0) s_slots = 0;
+    __syncthreads();
+    for (int t = tid; t < a.n_tiles; t += kSchedThreads) {
+        const uint2 r = a.ranges[t];
+        const uint32_t cnt = r.y - r.x;
+        const int m = parts(cnt);
+        atomicAdd(&s_cnt[length_bucket((cnt + m - 1) / (uint32_t)m)], (uint32_t)m);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < kSchedBuckets; ++b) {
+            s_pos[b] = run;
+            run += s_cnt[b];
+        }
+        *a.n_items = run;
+    }
+    __syncthreads();
+    for (int t = tid; t < a.n_tiles; t += kSchedThreads) {
+        const uint2 r = a.ranges[t];
+        const uint32_t cnt = r.y - r.x;
+        const int m = parts(cnt);
+        const int slot0 = m > 1 ? (int)atomicAdd(&s_slots, (uint32_t)m) : 0;
+        const uint32_t pos = atomicAdd(&s_pos[length_bucket((cnt + m - 1) / (uint32_t)m)], (uint32_t)m);
+        for (int k = 0; k < m; ++k) a.items[pos + k] = make_int4(t, k, m, slot0);
+    }
+}
+
 } // namespace
+
+void launch_schedule(const ScheduleArgs &a, cudaStream_t s) {
+    schedule_kernel<<<1, kSchedThreads, 0, s>>>(a);
+}
 
 void launch_scan_blocks(const BinArgs &a, cudaStream_t s) {
     scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(a);

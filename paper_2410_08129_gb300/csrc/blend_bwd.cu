@@ -18,7 +18,7 @@ bool run_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
             return false;
         configured = true;
     }
-    const int grid = persistent_grid((const void *)blend_bwd_kernel<TW, TH>, kBwdThreads, smem, b.total_tiles);
+    const int grid = persistent_grid((const void *)blend_bwd_kernel<TW, TH>, kBwdThreads, smem, a.max_items);
     blend_bwd_kernel<TW, TH><<<grid, kBwdThreads, smem, s>>>(b, a);
     return true;
 }

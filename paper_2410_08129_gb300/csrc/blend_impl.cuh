@@ -56,16 +56,19 @@ __device__ __forceinline__ float frag_depth(const float4 &c3, const float4 &c4, 
     return __fmul_rn(quad_eval(c3.x, c3.y, c3.z, c3.w, c4.x, c4.y, dx, dy), rD);
 }
 
-// Insertion into an ascending (depth, gid) list. Ties in depth keep the
-// earlier entry first; records are visited in ascending gid, so the order is
-// lexicographic in (depth, gid).
+// Insertion into a list sorted by (depth, gid). The new entry's gid exceeds
+// that of every listed entry of equal depth (records are visited in
+// ascending gid, and partial lists are merged in chunk order), so it goes
+// before the first strictly deeper entry; from there the rest of the list
+// shifts down by one, equal depths included, and the last entry drops out.
 template <int KMAX>
 __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KMAX], float z, uint32_t g) {
+    bool sw = false;
 #pragma unroll
     for (int i = 0; i < KMAX; ++i) {
         const float oz = cz[i];
         const uint32_t og = cg[i];
-        const bool sw = z < oz;
+        sw = sw || z < oz;
         cz[i] = sw ? z : oz;
         cg[i] = sw ? g : og;
         z = sw ? oz : z;
@@ -83,18 +86,24 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
     constexpr int WPR = TW / 8;  // footprints per tile row
     static_assert(TW % 8 == 0 && TH % WY == 0 && NT % 32 == 0, "unsupported blend shape");
+    constexpr int TP = TW * TH;
     __shared__ float4 s_rec[2][kBatch][kRecF4];
     __shared__ uint32_t s_gid[2][kBatch];
     __shared__ int s_item;
+    __shared__ int s_last;
     if (a.status[kStError] != 0) return;
+    const int n_items = min((int)*a.n_items, a.max_items);
 
-    // Persistent CTA: take (view, tile) items from the shared queue.
+    // Persistent CTA: take (view, tile, chunk) items from the shared queue.
     for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
     __syncthreads();
-    const int tile = s_item;
+    const int item = s_item;
     __syncthreads();
-    if (tile >= bt.total_tiles) break;
+    if (item >= n_items) break;
+    const int4 work = a.items[item];
+    const int tile = work.x, chunk_k = work.y, chunk_m = work.z, slot0 = work.w;
+    if (!item_ok(work, bt.total_tiles, a.slots)) continue;
     const ViewDesc &view = bt.v[view_of_tile(bt, tile)];
     const int local = tile - view.tile_off;
     const int tx = local % view.tiles_x, ty = local / view.tiles_x;
@@ -134,7 +143,7 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
         nall[p] = 0;
     }
 
-    const uint2 range = a.ranges[tile];
+    const uint2 range = chunk_range(a.ranges[tile], chunk_k, chunk_m);
     const int nbatches = (int)((range.y - range.x + kBatch - 1) / kBatch);
     auto batch_size = [&](int b) { return (int)min((uint32_t)kBatch, range.y - range.x - (uint32_t)b * kBatch); };
     auto load_ids = [&](int b) {
@@ -236,6 +245,70 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
             atomicAdd(a.stats + kStatKept, kept);
             atomicAdd(a.stats + kStatAdmitted, adm);
             atomicAdd(a.stats + kStatInserted, ins);
+        }
+    }
+
+    // A chunk of a split tile leaves its partial state (the sums over its
+    // fragments and its K nearest candidates); the tile's last chunk to
+    // finish merges all of them in chunk order. Chunks are ascending gid
+    // ranges, so inserting their core lists in chunk order keeps the
+    // (depth, gid) order of a single pass, and the merged core is the K
+    // nearest candidates of the whole list.
+    if (chunk_m > 1) {
+        const int W = 6 + 2 * K;
+        const int lx = px_i - tx * TW, ly0 = py_i0 - ty * TH;
+        float *part = a.partials + (size_t)(slot0 + chunk_k) * W * TP;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int lp = (ly0 + p) * TW + lx;
+            part[0 * TP + lp] = sA[p];
+            part[1 * TP + lp] = sR[p];
+            part[2 * TP + lp] = sG[p];
+            part[3 * TP + lp] = sB[p];
+            part[4 * TP + lp] = sP[p];
+            part[5 * TP + lp] = __int_as_float(nall[p]);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                if (k < KMAX - K) continue;
+                const int i = k - (KMAX - K);
+                part[(size_t)(6 + 2 * i) * TP + lp] = cz[p][k];
+                part[(size_t)(7 + 2 * i) * TP + lp] = __uint_as_float(cg[p][k]);
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(a.done + slot0, 1u) == (unsigned)(chunk_m - 1);
+        __syncthreads();
+        if (!s_last) continue;
+        __threadfence();
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                cz[p][k] = (k < KMAX - K) ? -INFINITY : INFINITY;
+                cg[p][k] = 0xffffffffu;
+            }
+            sA[p] = sR[p] = sG[p] = sB[p] = 0.f;
+            sP[p] = 1.f;
+            nall[p] = 0;
+        }
+        for (int c = 0; c < chunk_m; ++c) {
+            const float *pc = a.partials + (size_t)(slot0 + c) * W * TP;
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                const int lp = (ly0 + p) * TW + lx;
+                sA[p] += __ldcg(pc + 0 * TP + lp);
+                sR[p] += __ldcg(pc + 1 * TP + lp);
+                sG[p] += __ldcg(pc + 2 * TP + lp);
+                sB[p] += __ldcg(pc + 3 * TP + lp);
+                sP[p] *= __ldcg(pc + 4 * TP + lp);
+                nall[p] += __float_as_int(__ldcg(pc + 5 * TP + lp));
+                for (int i = 0; i < K; ++i) {
+                    const float z = __ldcg(pc + (size_t)(6 + 2 * i) * TP + lp);
+                    if (!(z < cz[p][KMAX - 1])) break;  // each list is ascending
+                    core_insert<KMAX>(cz[p], cg[p], z, __float_as_uint(__ldcg(pc + (size_t)(7 + 2 * i) * TP + lp)));
+                }
+            }
         }
     }
 
@@ -344,6 +417,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     __shared__ uint32_t s_next;
     __shared__ int s_item;
     const int K = a.prm.K;
+    const int n_items = min((int)*a.n_items, a.max_items);
     float4 *s_pa = smem;                 // g.xyz, k0
     float4 *s_pb = s_pa + TP;            // u.xyz, k1
     float4 *s_pc = s_pb + TP;            // last core depth, last core gid, mode, -
@@ -352,13 +426,18 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     float *s_cv = s_cw + (size_t)K * TP;                             // [K][TP] alpha_r T_r
     if (a.status[kStError] != 0) return;
 
-    // Persistent CTA: take (view, tile) items from the shared queue.
+    // Persistent CTA: take (view, tile, chunk) items from the shared queue.
+    // The adjoint of a chunk needs only the saved per-pixel state, so the
+    // chunks of a split tile are independent.
     for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
     __syncthreads();
-    const int tile = s_item;
+    const int item = s_item;
     __syncthreads();
-    if (tile >= bt.total_tiles) break;
+    if (item >= n_items) break;
+    const int4 work = a.items[item];
+    const int tile = work.x;
+    if (!item_ok(work, bt.total_tiles, a.max_items)) continue;  // (the adjoint uses no slots)
     const ViewDesc &view = bt.v[view_of_tile(bt, tile)];
     const int local = tile - view.tile_off;
     const int tx = local % view.tiles_x, ty = local / view.tiles_x;
@@ -372,7 +451,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
     const float bg0 = a.prm.bg[0], bg1 = a.prm.bg[1], bg2 = a.prm.bg[2];
     const size_t npix = (size_t)width * height;
-    const uint2 range = a.ranges[tile];
+    const uint2 range = chunk_range(a.ranges[tile], work.y, work.z);
 
     // Phase A: per-pixel adjoint state.
     for (int p = tid; p < TP; p += kBwdThreads) {
@@ -575,7 +654,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
 template <int KMAX, int TW, int TH, int PPT>
 void run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / PPT;
-    const int grid = persistent_grid((const void *)blend_fwd_kernel<KMAX, TW, TH, PPT>, NT, 0, b.total_tiles);
+    const int grid = persistent_grid((const void *)blend_fwd_kernel<KMAX, TW, TH, PPT>, NT, 0, a.max_items);
     blend_fwd_kernel<KMAX, TW, TH, PPT><<<grid, NT, 0, s>>>(b, a);
 }
 

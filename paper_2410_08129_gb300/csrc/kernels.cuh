@@ -21,6 +21,17 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
 constexpr int kMaxViews = HTGS_MAX_VIEWS;
 
+// Blend work items. A tile whose instance list is longer than the chunk size
+// C = max(kMinChunk, ceil(total / kChunkDiv)) is cut into m = ceil(count / C)
+// contiguous chunks processed by different CTAs; the forward's chunks leave
+// mergeable partial states in one of at most kMaxSlots slots. Items are
+// ordered by decreasing chunk length so that the long ones start first.
+constexpr uint32_t kMinChunk = 1024;
+constexpr uint32_t kChunkDiv = 2048;
+constexpr int kMaxSlots = 4096;
+constexpr int kSchedThreads = 1024;
+constexpr int kSchedBuckets = 64;
+
 struct ViewDesc {
     CamArgs cam;
     const float *means, *log_scales, *quats, *logits, *sh;
@@ -99,7 +110,7 @@ struct SortArgs {
     int passes;
     uint32_t *keys[2], *vals[2];
     uint32_t *ghist;       // kMaxPasses * kRadix
-    uint32_t *lookback;    // passes * n_sort_blocks * kRadix
+    unsigned long long *lookback;  // passes * n_sort_blocks * kRadix flag|count words
     uint32_t *tickets;     // kMaxPasses
     int n_sort_blocks;
     int *status;
@@ -112,10 +123,40 @@ struct RangeArgs {
     int n_tiles;
 };
 
+// Work item: (global tile, chunk k of m, first partial-state slot of the tile).
+struct ScheduleArgs {
+    const uint32_t *total;
+    const uint2 *ranges;
+    int n_tiles;
+    int slots_cap;         // partial-state slots available
+    int4 *items;           // n_tiles + slots_cap
+    uint32_t *n_items;
+};
+
+// A work item names an existing tile and a chunk k < m whose slots fit.
+__device__ __forceinline__ bool item_ok(int4 w, int n_tiles, int slots) {
+    return w.x >= 0 && w.x < n_tiles && w.z >= 1 && w.y >= 0 && w.y < w.z &&
+           (w.z == 1 || (w.w >= 0 && w.w + w.z <= slots));
+}
+
+// Instance range [start, end) of chunk k of m of a tile's list.
+__device__ __forceinline__ uint2 chunk_range(uint2 r, int k, int m) {
+    if (m <= 1) return r;
+    const uint32_t per = (r.y - r.x + (uint32_t)m - 1) / (uint32_t)m;
+    const uint32_t a = min(r.x + (uint32_t)k * per, r.y);
+    return make_uint2(a, min(a + per, r.y));
+}
+
 struct BlendFwdArgs {
     const float4 *rec;
     const uint32_t *vals;  // sorted record indices
     const uint2 *ranges;
+    const int4 *items;
+    const uint32_t *n_items;
+    float *partials;       // slots * (6 + 2K) * tile pixels
+    unsigned int *done;    // per split tile (at its first slot): chunks finished
+    int max_items;         // bound on the item count (grid size cap)
+    int slots;             // partial-state slots
     const int *status;
     unsigned int *work;    // persistent-kernel work counter (zeroed per render)
     TileArgs tiles;
@@ -127,6 +168,9 @@ struct BlendBwdArgs {
     const float4 *rec;
     const uint32_t *vals;
     const uint2 *ranges;
+    const int4 *items;
+    const uint32_t *n_items;
+    int max_items;
     const int *status;
     unsigned int *work;
     TileArgs tiles;
@@ -144,6 +188,8 @@ void launch_emit(const Batch &b, const BinArgs &a, cudaStream_t s);
 // Returns the buffer index (0 or 1) holding the result.
 int launch_sort(const SortArgs &a, cudaStream_t s);
 void launch_ranges(RangeArgs a, cudaStream_t s);
+// Blend work items from the tile ranges (one CTA).
+void launch_schedule(const ScheduleArgs &a, cudaStream_t s);
 
 // Persistent blend kernels over the batch's (view, tile) items; return false
 // when (K, tile shape, px/thread) has no compiled instance.

@@ -47,17 +47,17 @@ extern "C" htgs_status htgs_render_static(const htgs_gaussians *gaussians, const
     htgs_status st = htgs_workspace_size(gaussians->n, cam, params, launch, 0, &base, nullptr);
     if (st != HTGS_OK) return st;
     if (base > kStaticBytes) return HTGS_ERR_WORKSPACE;
-    // Largest instance capacity whose workspace fits (about 17 bytes each).
-    int64_t cap = (int64_t)((kStaticBytes - base) / 17);
-    size_t need = 0;
-    for (int tries = 0; tries < 64; ++tries) {
-        st = htgs_workspace_size(gaussians->n, cam, params, launch, cap, &need, nullptr);
+    // Largest instance capacity whose workspace fits: the size grows
+    // monotonically with the capacity, so bisect (host arithmetic only).
+    int64_t lo = 0, hi = (int64_t)(kStaticBytes / 16) + 1;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        size_t need = 0;
+        st = htgs_workspace_size(gaussians->n, cam, params, launch, mid, &need, nullptr);
         if (st != HTGS_OK) return st;
-        if (need <= kStaticBytes) break;
-        cap -= (int64_t)((need - kStaticBytes) / 16 + 1024);
-        if (cap <= 0) return HTGS_ERR_WORKSPACE;
+        if (need <= kStaticBytes) lo = mid; else hi = mid;
     }
-    if (need > kStaticBytes) return HTGS_ERR_WORKSPACE;
+    const int64_t cap = lo;
     void *ws = nullptr;
     st = scratch_address(&ws);
     if (st != HTGS_OK) return st;

@@ -14,6 +14,14 @@ from . import binding as B
 FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
+def _grown_capacity(needed: int, current: int) -> int:
+    """Instance capacity after an overflow: 25% headroom, at most the ABI's limit."""
+    if needed > B.HTGS_MAX_CAPACITY:
+        raise B.HTGSError(B.HTGS_ERR_OVERFLOW, f"{needed} tile instances exceed the {B.HTGS_MAX_CAPACITY} limit; "
+                          "split the views over several batches")
+    return min(max(int(needed * 1.25) + 1024, current), B.HTGS_MAX_CAPACITY)
+
+
 @dataclasses.dataclass
 class GaussianTensors:
     means: torch.Tensor
@@ -65,7 +73,7 @@ class Renderer:
         self.saved = torch.empty(max(saved // 4, 1), dtype=torch.float32, device=self.device)
 
     def grow(self, needed: int):
-        self.capacity = max(int(needed * 1.25) + 1024, self.capacity)
+        self.capacity = _grown_capacity(needed, self.capacity)
         self._alloc()
 
     def image_buffer(self):
@@ -184,7 +192,7 @@ class BatchRenderer:
                 return self.images
             st, inst = B.htgs_get_error(self.workspace, stream)
             if st == B.HTGS_ERR_OVERFLOW:
-                self.capacity = max(int(inst * 1.25) + 1024, self.capacity)
+                self.capacity = _grown_capacity(inst, self.capacity)
                 self._alloc()
                 continue
             B._check(st, "htgs_render_batch (device)")

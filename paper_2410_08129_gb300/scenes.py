@@ -224,12 +224,18 @@ def config3(n: int = 500_000, seed: int = 2):
     logits by N(0, 0.1)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     scene = small_box_scene(n, seed, rng=rng)
-    target = Scene(scene.means + rng.normal(0.0, 0.01, scene.means.shape).astype(np.float32),
-                   scene.log_scales.copy(), scene.quats.copy(),
-                   scene.opacity_logits + rng.normal(0.0, 0.1, n).astype(np.float32),
-                   scene.sh.copy(), scene.sh_degree)
+    target = perturbed(scene, rng)
     cam = identity_camera(1200, 800, 1200.0)
     return scene, target, cam, Params(K=8)
+
+
+def perturbed(scene: Scene, rng: np.random.Generator) -> Scene:
+    """Target Gaussians of a training step: means + N(0, 0.01), logits + N(0, 0.1)."""
+    n = scene.n
+    return Scene(scene.means + rng.normal(0.0, 0.01, scene.means.shape).astype(np.float32),
+                 scene.log_scales.copy(), scene.quats.copy(),
+                 scene.opacity_logits + rng.normal(0.0, 0.1, n).astype(np.float32),
+                 scene.sh.copy(), scene.sh_degree)
 
 
 def config4_views(n_views: int = 32, seed: int = 3):
@@ -254,6 +260,21 @@ def config4_scene(n: int = 3_000_000, seed: int = 3) -> Scene:
 
 def config4_multi_scene_sizes():
     return [50_000, 100_000, 250_000, 500_000, 750_000, 1_000_000, 1_500_000, 2_000_000]
+
+
+def config4_multi(seed: int = 5, sizes=None):
+    """Eight scenes of uneven size (config-1 distribution), one 1280x720 view
+    each from a camera on the 6 m sphere around the box centre."""
+    sizes = sizes if sizes is not None else config4_multi_scene_sizes()
+    rng = np.random.Generator(np.random.PCG64(seed + 2000))
+    centre = np.array([0.0, 0.0, 3.0])
+    out = []
+    for i, n in enumerate(sizes):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        cam = fov_camera(look_at(centre + 6.0 * d, centre), 1280, 720, 60.0, 0.2)
+        out.append((small_box_scene(n, seed * 100 + i), cam))
+    return out
 
 
 def config5(n: int = 6_000_000, seed: int = 4, frac_flat: float = 0.05,

@@ -115,6 +115,41 @@ def test_k_values(K):
     assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS
 
 
+def test_core_ties_broken_by_gid():
+    """Exact depth ties (duplicated Gaussians give bit-equal depths in FP32
+    and FP64): the core is the K smallest (depth, gid) pairs. Gid order B, B,
+    A with A nearer and K = 2 must give (A, first B), also after A evicts a
+    tied entry; then a scene where every Gaussian appears three times."""
+    base = scenes.small_box_scene(2, seed=31)
+    base.means[:] = [[0.0, 0.0, 3.0], [0.0, 0.0, 2.5]]
+    base.log_scales[:] = np.float32(-1.5)
+    base.opacity_logits[:] = np.float32(0.0)
+    tri = base.subset(np.array([0, 0, 1, 0]))          # gids: B B A B
+    cam = scenes.identity_camera(32, 32, 40.0).rounded()
+    prm = scenes.Params(K=2)
+    img, r, g = gpu_render(tri, cam, prm)
+    sv = saved_planes(r, cam, 2)
+    _, d = oracle.render(tri.astype(np.float64), cam, prm, diagnostics=True)
+    both = d["n_core"] == 2
+    assert both.sum() > 0
+    np.testing.assert_array_equal(sv["core_gid"][both], np.broadcast_to([2, 0], (int(both.sum()), 2)))
+    np.testing.assert_array_equal(sv["core_gid"][both], d["core_gid"][both])
+
+    scene = scenes.small_box_scene(40, seed=32, sh_degree=1)
+    scene.log_scales += np.float32(0.5)
+    order = np.random.default_rng(33).permutation(np.repeat(np.arange(40), 3))
+    dup = scene.subset(order)
+    cam = scenes.identity_camera(64, 48, 60.0).rounded()
+    for K in (2, 4, 8):
+        prm = scenes.Params(K=K)
+        img, r, g = gpu_render(dup, cam, prm)
+        sv = saved_planes(r, cam, K)
+        _, d = oracle.render(dup.astype(np.float64), cam, prm, diagnostics=True)
+        ok = d["ambiguous"] == 0
+        np.testing.assert_array_equal(sv["n_core"][ok], d["n_core"][ok])
+        np.testing.assert_array_equal(sv["core_gid"][ok], d["core_gid"][ok])
+
+
 def test_ragged_image_and_big_splats():
     """Image sizes that are not tile multiples; splats much larger than a tile."""
     scene = scenes.small_box_scene(60, seed=6, sh_degree=2)
