@@ -91,6 +91,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def recorded_traffic():
+    """DRAM bytes per launch of the forward blend on the headline workload,
+    as measured by ncu (profiles/blend_fwd_traffic.json); None when the
+    kernel's sources changed since the counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "blend_fwd_traffic.json")
+    try:
+        with open(prof) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in rec["sources"]:
+            with open(os.path.join(ROOT, "paper_2410_08129_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    return rec.get("bytes_per_launch_1080p_1M") if h.hexdigest() == rec.get("sources_sha256") else None
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -555,14 +573,7 @@ def main():
     blend_s = float(np.mean(blend_ms)) / 1e3
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6
     achieved = alg / blend_s
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "blend_fwd_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                traffic = json.load(f).get("bytes_per_launch_1080p_1M")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = recorded_traffic()
 
     batched = None
     if not args.no_batched:
