@@ -109,6 +109,24 @@ def recorded_traffic():
     return rec.get("bytes_per_launch_1080p_1M") if h.hexdigest() == rec.get("sources_sha256") else None
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Largest value of x over the ranks of the default process group (the
+    job's time is that of its slowest rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput of replicas: every rank processes units_per_rank
+    units; the job ends with its slowest rank (max_ms)."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -207,7 +225,7 @@ def plain_vs_batched(gs, tgs, cams, prm, steps, warmup, tune_views=None, graph=T
     launch, tune_ms = autotune(step_for_launch, warmup=1, repeats=2)
     tune_s = time.perf_counter() - t0
     torch.cuda.empty_cache()
-    tile, ppt = (launch.tile_w, launch.tile_h), launch.px_per_thread
+    tile, ppt, sbatch = (launch.tile_w, launch.tile_h), launch.px_per_thread, launch.smem_batch
 
     # -- plain: one Renderer per view ------------------------------------------
     rs = [Renderer(c, prm, g.n, launch=launch) for g, c in zip(gs, cams)]
@@ -329,8 +347,9 @@ def plain_vs_batched(gs, tgs, cams, prm, steps, warmup, tune_views=None, graph=T
     return {
         "views": n_views, "gaussians": [int(g.n) for g in distinct.values()],
         "pixels": int(sum(c.width * c.height for c in cams)), "instances": int(sum(inst)),
-        "launch": {"tile": f"{tile[0]}x{tile[1]}", "px_per_thread": int(ppt),
-                   "autotune_ms_per_step": {f"{t[0]}x{t[1]}/ppt{p}": round(v, 3) for (t, p), v in tune_ms.items()},
+        "launch": {"tile": f"{tile[0]}x{tile[1]}", "px_per_thread": int(ppt), "smem_batch": int(sbatch),
+                   "autotune_ms_per_step": {f"{t[0]}x{t[1]}/ppt{p}/b{b}": round(v, 3)
+                                            for (t, p, b), v in tune_ms.items()},
                    "autotune_views": len(sub), "autotune_s": round(tune_s, 1)},
         "batches": len(groups), "cuda_graph": bool(graph),
         "fwd": {"plain_frames_per_s": n_views * 1e3 / ms["plain_fwd"],
@@ -444,11 +463,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     stream = torch.cuda.current_stream()
     peaks, peak_src = _peaks()
@@ -490,7 +505,7 @@ def main():
     counters = B.htgs_get_counters(r.workspace)
     total_ms = max_over_ranks(t_start.elapsed_time(t_end))
     ms_per_step = total_ms / args.steps
-    fps = world * args.steps / (total_ms / 1e3)
+    fps = job_throughput(args.steps, world, total_ms)
 
     # ---- end to end through the C ABI with host buffers --------------------
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
@@ -516,7 +531,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
-    e2e_fps = world * args.steps / (e2e_ms / 1e3)
+    e2e_fps = job_throughput(args.steps, world, e2e_ms)
 
     # ---- training step: render + L1 + backward (500k Gaussians, 1200x800) --
     tscene, ttarget, tcam, tprm = scenes.config3(seed=2 + rank)
@@ -596,7 +611,7 @@ def main():
         "phases_ms": {"preprocess": float(np.mean(pre_ms)), "binning_sort": float(np.mean(bin_ms)),
                       "blend": float(np.mean(blend_ms))},
         "instances": inst, "counters": counters,
-        "fwd_bwd": {"value": 1e3 / train_ms * world, "unit": "steps/s", "ms_per_step": train_ms,
+        "fwd_bwd": {"value": job_throughput(1, world, train_ms), "unit": "steps/s", "ms_per_step": train_ms,
                     "workload": "500k Gaussians (box distribution), 1200x800, K=8: render + L1 + backward",
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
                     "grads_finite": gfinite},

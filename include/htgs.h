@@ -103,6 +103,8 @@ typedef struct {
     int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 16x8 or 8x8 */
     int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4 */
     int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */
+    int32_t smem_batch;       /* records the forward blend stages per shared-memory batch:
+                                 32, 64 or 128 (default, also for 0) */
     void *events[6];
 } htgs_launch;
 

@@ -31,7 +31,10 @@
 
 namespace htgs {
 
-constexpr int kBatch = 64;
+// Largest number of records the forward stages per shared-memory batch
+// (the batch in use, htgs_launch.smem_batch, is 32, 64 or 128).
+constexpr int kMaxBatch = 128;
+
 constexpr int kBwdThreads = 256;
 
 // Alpha of one record at a pixel from its (Q, D) pair, evaluated identically
@@ -59,21 +62,22 @@ __device__ __forceinline__ float frag_depth(const float4 &c3, const float4 &c4, 
 // Insertion into a list sorted by (depth, gid). The new entry's gid exceeds
 // that of every listed entry of equal depth (records are visited in
 // ascending gid, and partial lists are merged in chunk order), so it goes
-// before the first strictly deeper entry; from there the rest of the list
-// shifts down by one, equal depths included, and the last entry drops out.
+// before the first strictly deeper entry, the entries from there on shift
+// down by one (equal depths included) and the last one drops out. The
+// predicates "new entry is nearer than slot i" are monotone along the list
+// and independent of each other, so all slots update in parallel.
 template <int KMAX>
 __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KMAX], float z, uint32_t g) {
-    bool sw = false;
+    bool nearer[KMAX];
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-        const float oz = cz[i];
-        const uint32_t og = cg[i];
-        sw = sw || z < oz;
-        cz[i] = sw ? z : oz;
-        cg[i] = sw ? g : og;
-        z = sw ? oz : z;
-        g = sw ? og : g;
+    for (int i = 0; i < KMAX; ++i) nearer[i] = z < cz[i];
+#pragma unroll
+    for (int i = KMAX - 1; i > 0; --i) {
+        cz[i] = nearer[i] ? (nearer[i - 1] ? cz[i - 1] : z) : cz[i];
+        cg[i] = nearer[i] ? (nearer[i - 1] ? cg[i - 1] : g) : cg[i];
     }
+    cz[0] = nearer[0] ? z : cz[0];
+    cg[0] = nearer[0] ? g : cg[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -87,8 +91,9 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int WPR = TW / 8;  // footprints per tile row
     static_assert(TW % 8 == 0 && TH % WY == 0 && NT % 32 == 0, "unsupported blend shape");
     constexpr int TP = TW * TH;
-    __shared__ float4 s_rec[2][kBatch][kRecF4];
-    __shared__ uint32_t s_gid[2][kBatch];
+    __shared__ float4 s_rec[2 * kMaxBatch * kRecF4];  // two batches of B records
+    __shared__ uint32_t s_gid[2 * kMaxBatch];
+    const int B = a.tiles.batch;
     __shared__ int s_item;
     __shared__ int s_last;
     if (a.status[kStError] != 0) return;
@@ -144,18 +149,21 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     }
 
     const uint2 range = chunk_range(a.ranges[tile], chunk_k, chunk_m);
-    const int nbatches = (int)((range.y - range.x + kBatch - 1) / kBatch);
-    auto batch_size = [&](int b) { return (int)min((uint32_t)kBatch, range.y - range.x - (uint32_t)b * kBatch); };
+    const int nbatches = (int)((range.y - range.x + B - 1) / B);
+    auto batch_size = [&](int b) { return (int)min((uint32_t)B, range.y - range.x - (uint32_t)b * B); };
     auto load_ids = [&](int b) {
-        const uint32_t base = range.x + (uint32_t)b * kBatch;
+        const uint32_t base = range.x + (uint32_t)b * B;
         const int nb = batch_size(b);
-        for (int k = tid; k < nb; k += NT) s_gid[b & 1][k] = a.vals[base + k];
+        uint32_t *ids = s_gid + (b & 1) * B;
+        for (int k = tid; k < nb; k += NT) ids[k] = a.vals[base + k];
     };
     auto issue = [&](int b) {
         const int nb = batch_size(b);
+        const uint32_t *ids = s_gid + (b & 1) * B;
+        float4 *dst = s_rec + (size_t)(b & 1) * B * kRecF4;
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
-            cp_async16(&s_rec[b & 1][j][f], a.rec + (size_t)s_gid[b & 1][j] * kRecF4 + f);
+            cp_async16(dst + k, a.rec + (size_t)ids[j] * kRecF4 + f);
         }
         cp_async_commit();
     };
@@ -175,8 +183,8 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
         }
         __syncthreads();
         const int nb = batch_size(b);
-        const float4(*rec)[kRecF4] = s_rec[b & 1];
-        const uint32_t *gids = s_gid[b & 1];
+        const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(s_rec + (size_t)(b & 1) * B * kRecF4);
+        const uint32_t *gids = s_gid + (b & 1) * B;
         for (int c = 0; c < nb; c += 32) {
             bool hit = false;
             if (c + lane < nb) {

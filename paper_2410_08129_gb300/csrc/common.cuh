@@ -33,6 +33,7 @@ struct TileArgs {
     int n_tiles;
     int tile_bits;   // bits of the sort key holding the tile id
     int depth_bits;  // low key bits holding quantised depth
+    int batch;       // records per shared-memory batch of the forward blend
 };
 
 // Per-Gaussian blend record: 32 floats = 128 bytes = 8 float4.

@@ -2,7 +2,7 @@
 // Sec. 3.1 scene representation, Sec. 3.2 Eq. (3) T' = V P M T, the tight
 // screen bounding box and the opacity-aware cutoff).
 //
-// One thread per Gaussian. The forward writes the 96-byte blend record (see
+// One thread per Gaussian. The forward writes the 128-byte blend record (see
 // common.cuh), the covered tile rectangle and the tile count; the backward
 // turns the per-Gaussian gradient accumulators of the blend adjoint into
 // gradients of the means, log-scales, quaternions, opacity logits and SH.

@@ -51,7 +51,7 @@ def test_library_loads_and_host_entry_points_work(lib_path):
     assert B.htgs_status_string(B.HTGS_ERR_OVERFLOW) != B.htgs_status_string(B.HTGS_OK)
 
 
-@pytest.mark.parametrize("bad", ["K", "capacity", "tile", "n", "alpha_max", "size"])
+@pytest.mark.parametrize("bad", ["K", "capacity", "tile", "batch", "n", "alpha_max", "size"])
 def test_host_side_argument_checks(lib_path, bad):
     from paper_2410_08129_gb300 import binding as B
     _, cam, prm, tile = scenes.config1()
@@ -64,6 +64,9 @@ def test_host_side_argument_checks(lib_path, bad):
         expect = B.HTGS_ERR_INVALID_ARG
     elif bad == "tile":
         launch = B.c_launch((12, 12))
+        expect = B.HTGS_ERR_NOT_SUPPORTED
+    elif bad == "batch":
+        launch = B.c_launch(tile, smem_batch=48)
         expect = B.HTGS_ERR_NOT_SUPPORTED
     elif bad == "n":
         n = -1

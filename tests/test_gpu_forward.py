@@ -95,6 +95,22 @@ def test_launch_shapes_agree(cfg1, tile, ppt):
     assert np.abs(img2 - img).max() <= 1e-6
 
 
+@pytest.mark.parametrize("batch", [32, 128])
+def test_smem_batch_sizes_agree(batch):
+    """The records staged per shared-memory batch change only the staging:
+    the traversal order and arithmetic are the same, so the image is
+    bit-identical (including tiles split into chunks)."""
+    scene = scenes.small_box_scene(9000, seed=41, sh_degree=1)
+    scene.log_scales += np.float32(0.7)
+    cam = scenes.identity_camera(96, 80, 80.0).rounded()
+    prm = scenes.Params(K=8)
+    ref, *_ = gpu_render(scene, cam, prm)
+    g = GaussianTensors.from_scene(scene)
+    r = Renderer(cam, prm, scene.n, launch=B.c_launch((16, 16), 1, smem_batch=batch))
+    img = r.forward(g).cpu().numpy().astype(np.float64)
+    assert np.array_equal(img, ref)
+
+
 def test_deterministic(cfg1):
     scene, cam, prm, tile, img, r, g, *_ = cfg1
     a = r.forward(g).cpu().numpy()
