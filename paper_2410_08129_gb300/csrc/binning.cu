@@ -9,6 +9,10 @@
 //   onesweep     one stable scatter per 8-bit digit; the block prefix comes
 //                from a decoupled look-back whose waits are bounded
 //   ranges       [start, end) of every tile in the sorted keys
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -393,6 +397,21 @@ void launch_ranges(RangeArgs a, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ranges_kernel<<<sms * 8, 256, 0, s>>>(a);
+}
+
+bool allow_dynamic_smem(const void *kernel, size_t bytes) {
+    // Once per (kernel, device): the attribute persists, and repeating the
+    // call on every launch (possibly inside a stream capture) is avoidable.
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return true;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return false;
+    done.insert({kernel, dev});
+    return true;
 }
 
 int persistent_grid(const void *kernel, int threads, size_t dyn_smem, int items) {

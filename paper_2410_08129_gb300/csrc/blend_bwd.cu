@@ -10,14 +10,8 @@ namespace {
 template <int TW, int TH>
 bool run_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     const size_t smem = bwd_smem_bytes(TW * TH, a.prm.K);
-    // Raise the dynamic shared-memory limit once per process and device.
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(blend_bwd_kernel<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bwd_smem_bytes(TW * TH, HTGS_MAX_K)) != cudaSuccess)
-            return false;
-        configured = true;
-    }
+    if (!allow_dynamic_smem((const void *)blend_bwd_kernel<TW, TH>, bwd_smem_bytes(TW * TH, HTGS_MAX_K)))
+        return false;
     const int grid = persistent_grid((const void *)blend_bwd_kernel<TW, TH>, kBwdThreads, smem, a.max_items);
     blend_bwd_kernel<TW, TH><<<grid, kBwdThreads, smem, s>>>(b, a);
     return true;

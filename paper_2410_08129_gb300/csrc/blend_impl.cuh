@@ -31,9 +31,11 @@
 
 namespace htgs {
 
-// Largest number of records the forward stages per shared-memory batch
-// (the batch in use, htgs_launch.smem_batch, is 32, 64 or 128).
-constexpr int kMaxBatch = 128;
+// Dynamic shared memory of the forward: three staging buffers of B records
+// and their ids (B = htgs_launch.smem_batch: 32, 64 or 128).
+__host__ __device__ inline size_t fwd_smem_bytes(int B) {
+    return (size_t)3 * B * (kRecF4 * sizeof(float4) + sizeof(uint32_t));
+}
 
 constexpr int kBwdThreads = 256;
 
@@ -91,9 +93,10 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int WPR = TW / 8;  // footprints per tile row
     static_assert(TW % 8 == 0 && TH % WY == 0 && NT % 32 == 0, "unsupported blend shape");
     constexpr int TP = TW * TH;
-    __shared__ float4 s_rec[2 * kMaxBatch * kRecF4];  // two batches of B records
-    __shared__ uint32_t s_gid[2 * kMaxBatch];
+    extern __shared__ float4 s_dyn[];
     const int B = a.tiles.batch;
+    float4 *const s_rec = s_dyn;                                                   // [3][B][kRecF4]
+    uint32_t *const s_gid = reinterpret_cast<uint32_t *>(s_dyn + 3 * B * kRecF4);  // [3][B]
     __shared__ int s_item;
     __shared__ int s_last;
     if (a.status[kStError] != 0) return;
@@ -151,40 +154,36 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     const uint2 range = chunk_range(a.ranges[tile], chunk_k, chunk_m);
     const int nbatches = (int)((range.y - range.x + B - 1) / B);
     auto batch_size = [&](int b) { return (int)min((uint32_t)B, range.y - range.x - (uint32_t)b * B); };
-    auto load_ids = [&](int b) {
-        const uint32_t base = range.x + (uint32_t)b * B;
-        const int nb = batch_size(b);
-        uint32_t *ids = s_gid + (b & 1) * B;
-        for (int k = tid; k < nb; k += NT) ids[k] = a.vals[base + k];
-    };
+    // Stage batch b into buffer b % 3: each thread fetches the ids of the
+    // records it copies (8 threads per record read the same id), so no
+    // barrier separates the id loads from the copies.
     auto issue = [&](int b) {
         const int nb = batch_size(b);
-        const uint32_t *ids = s_gid + (b & 1) * B;
-        float4 *dst = s_rec + (size_t)(b & 1) * B * kRecF4;
+        const uint32_t base = range.x + (uint32_t)b * B;
+        const int buf = b % 3;
+        float4 *dst = s_rec + (size_t)buf * B * kRecF4;
+        uint32_t *ids = s_gid + buf * B;
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
-            cp_async16(dst + k, a.rec + (size_t)ids[j] * kRecF4 + f);
+            const uint32_t gid = a.vals[base + j];
+            if (f == 0) ids[j] = gid;
+            cp_async16(dst + k, a.rec + (size_t)gid * kRecF4 + f);
         }
         cp_async_commit();
     };
-    if (nbatches > 0) {
-        load_ids(0);
-        __syncthreads();
-        issue(0);
-    }
+    // Two batches in flight, one barrier per batch: after it, batch b is
+    // visible to every thread and every thread has finished batch b - 1,
+    // whose buffer the copies of batch b + 2 then overwrite.
+    if (nbatches > 0) issue(0);
+    if (nbatches > 1) issue(1);
     for (int b = 0; b < nbatches; ++b) {
-        if (b + 1 < nbatches) {
-            load_ids(b + 1);
-            __syncthreads();
-            issue(b + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+        if (b + 1 < nbatches) cp_async_wait<1>();
+        else cp_async_wait<0>();
         __syncthreads();
+        if (b + 2 < nbatches) issue(b + 2);
         const int nb = batch_size(b);
-        const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(s_rec + (size_t)(b & 1) * B * kRecF4);
-        const uint32_t *gids = s_gid + (b & 1) * B;
+        const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(s_rec + (size_t)(b % 3) * B * kRecF4);
+        const uint32_t *gids = s_gid + (b % 3) * B;
         for (int c = 0; c < nb; c += 32) {
             bool hit = false;
             if (c + lane < nb) {
@@ -234,7 +233,6 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
                 }
             }
         }
-        __syncthreads();
     }
 
     // Work counters: one atomic per warp.
@@ -660,18 +658,22 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
 // Dispatch over tile shape and pixels per thread for one KMAX.
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT>
-void run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
+bool run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / PPT;
-    const int grid = persistent_grid((const void *)blend_fwd_kernel<KMAX, TW, TH, PPT>, NT, 0, a.max_items);
-    blend_fwd_kernel<KMAX, TW, TH, PPT><<<grid, NT, 0, s>>>(b, a);
+    const void *fn = (const void *)blend_fwd_kernel<KMAX, TW, TH, PPT>;
+    const size_t smem = fwd_smem_bytes(a.tiles.batch);
+    if (!allow_dynamic_smem(fn, fwd_smem_bytes(128))) return false;
+    const int grid = persistent_grid(fn, NT, smem, a.max_items);
+    blend_fwd_kernel<KMAX, TW, TH, PPT><<<grid, NT, smem, s>>>(b, a);
+    return true;
 }
 
 template <int KMAX, int PPT>
 bool dispatch_shape_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
-    if (tw == 16 && th == 16) { run_fwd<KMAX, 16, 16, PPT>(b, a, s); return true; }
-    if (tw == 16 && th == 8 && PPT <= 2) { run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2)>(b, a, s); return true; }
-    if (tw == 8 && th == 8 && PPT <= 2) { run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(b, a, s); return true; }
+    if (tw == 16 && th == 16) return run_fwd<KMAX, 16, 16, PPT>(b, a, s);
+    if (tw == 16 && th == 8 && PPT <= 2) return run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2)>(b, a, s);
+    if (tw == 8 && th == 8 && PPT <= 2) return run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(b, a, s);
     return false;
 }
 

@@ -198,5 +198,7 @@ bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s);
 
 // CTAs per SM the persistent kernels are launched with (occupancy query).
 int persistent_grid(const void *kernel, int threads, size_t dyn_smem, int items);
+// Raises a kernel's dynamic shared-memory limit to `bytes` (once per device).
+bool allow_dynamic_smem(const void *kernel, size_t bytes);
 
 } // namespace htgs
