@@ -28,7 +28,7 @@ struct Layout {
     // byte offsets inside the workspace
     size_t status, stats, total, work, ghist, tickets, ranges, lookback, n_items, done, zero_end;
     size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, end;
-    int n_blocks, n_sort_blocks, passes, slots_cap, max_items;
+    int n_blocks, n_sort_blocks, passes, digit_bits, slots_cap, max_items;
     TileArgs tiles;
     int64_t n_rec;
 };
@@ -90,17 +90,20 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     L.n_blocks = (int)((n_rec + kPreThreads - 1) / kPreThreads);
     L.n_sort_blocks = (int)((capacity + kSortTile - 1) / kSortTile);
     if (L.n_sort_blocks < 1) L.n_sort_blocks = 1;
-    L.passes = (bits + kRadixBits - 1) / kRadixBits;
+    // Fewest passes of at most kMaxRadixBits bits, the bits split evenly.
+    L.passes = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
+    L.digit_bits = (bits + L.passes - 1) / L.passes;
     size_t o = 0;
     // Zero-initialised region (one memset per render).
     L.status = o; o = align_up(o + kStSlots * sizeof(int));
     L.stats = o; o = align_up(o + kStatSlots * sizeof(unsigned long long));
     L.total = o; o = align_up(o + 4 * sizeof(uint32_t));
     L.work = o; o = align_up(o + 4 * sizeof(uint32_t));
-    L.ghist = o; o = align_up(o + kMaxPasses * kRadix * sizeof(uint32_t));
+    L.ghist = o; o = align_up(o + kMaxPasses * kMaxRadix * sizeof(uint32_t));
     L.tickets = o; o = align_up(o + kMaxPasses * sizeof(uint32_t));
     L.ranges = o; o = align_up(o + (size_t)n_tiles * sizeof(uint2));
-    L.lookback = o; o = align_up(o + (size_t)L.passes * L.n_sort_blocks * kRadix * sizeof(unsigned long long));
+    L.lookback = o;
+    o = align_up(o + (size_t)L.passes * L.n_sort_blocks * ((size_t)1 << L.digit_bits) * sizeof(unsigned long long));
     // Split-tile slots: enough for chunks of kMinChunk over the whole capacity, at most kMaxSlots.
     L.slots_cap = (int)std::min<int64_t>(kMaxSlots, 2 * ((capacity + kMinChunk - 1) / kMinChunk) + 2);
     L.max_items = (int)(n_tiles + L.slots_cap);
@@ -260,7 +263,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     launch_emit(b, bin, s);
 
     SortArgs so{};
-    so.capacity = capacity; so.total = total; so.passes = L.passes;
+    so.capacity = capacity; so.total = total; so.passes = L.passes; so.digit_bits = L.digit_bits;
     so.keys[0] = at<uint32_t>(workspace, L.keys0); so.vals[0] = at<uint32_t>(workspace, L.vals0);
     so.keys[1] = at<uint32_t>(workspace, L.keys1); so.vals[1] = at<uint32_t>(workspace, L.vals1);
     so.ghist = at<uint32_t>(workspace, L.ghist);

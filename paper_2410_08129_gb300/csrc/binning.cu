@@ -6,8 +6,11 @@
 //   emit         one thread group per Gaussian writes (tile key, gid) for each
 //                covered tile, load-balanced across the lanes of a warp
 //   histogram    digit histograms of every radix pass in one read of the keys
-//   onesweep     one stable scatter per 8-bit digit; the block prefix comes
-//                from a decoupled look-back whose waits are bounded
+//   onesweep     one stable scatter per digit (the key bits split evenly into
+//                the fewest passes of at most 9 bits); the block prefix comes
+//                from a decoupled look-back whose waits are bounded, and each
+//                block orders its items by digit in shared memory first so
+//                that its stores are runs of consecutive addresses
 //   ranges       [start, end) of every tile in the sorted keys
 #include <mutex>
 #include <set>
@@ -155,18 +158,20 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
 // Radix sort: digit histograms for all passes in one read.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) histogram_kernel(SortArgs a) {
-    __shared__ uint32_t h[kMaxPasses * kRadix];
-    for (int k = threadIdx.x; k < a.passes * kRadix; k += kSortThreads) h[k] = 0;
+    __shared__ uint32_t h[kMaxPasses * kMaxRadix];
+    const int R = 1 << a.digit_bits;
+    for (int k = threadIdx.x; k < a.passes * kMaxRadix; k += kSortThreads) h[k] = 0;
     __syncthreads();
     const uint32_t total = *a.total;
     const uint32_t *keys = a.keys[0];
     for (uint32_t idx = blockIdx.x * kSortThreads + threadIdx.x; idx < total;
          idx += gridDim.x * kSortThreads) {
         const uint32_t k = keys[idx];
-        for (int p = 0; p < a.passes; ++p) atomicAdd(&h[p * kRadix + ((k >> (p * kRadixBits)) & (kRadix - 1))], 1u);
+        for (int p = 0; p < a.passes; ++p)
+            atomicAdd(&h[p * kMaxRadix + ((k >> (p * a.digit_bits)) & (uint32_t)(R - 1))], 1u);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < a.passes * kRadix; k += kSortThreads)
+    for (int k = threadIdx.x; k < a.passes * kMaxRadix; k += kSortThreads)
         if (h[k]) atomicAdd(&a.ghist[k], h[k]);
 }
 
@@ -183,37 +188,61 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int pass, int src) {
-    __shared__ uint32_t s_whist[kSortWarps][kRadix];
-    __shared__ uint32_t s_base[kRadix];
-    __shared__ uint32_t s_scan[kRadix];
+    // s_whist (per-warp digit counts, then their prefixes) and s_k (the block's
+    // keys in digit order) are alive at different times and share storage.
+    __shared__ uint32_t s_kw[kSortTile > kSortWarps * kMaxRadix ? kSortTile : kSortWarps * kMaxRadix];
+    __shared__ uint32_t s_v[kSortTile];
+    __shared__ uint32_t s_base[kMaxRadix];    // global position of the block's first item of each digit
+    __shared__ uint32_t s_scan[kMaxRadix];    // global exclusive digit offsets
+    __shared__ uint32_t s_cnt[kMaxRadix];     // block digit counts
+    __shared__ uint32_t s_bstart[kMaxRadix];  // block-local exclusive digit offsets
     __shared__ uint32_t s_wsum[kSortWarps];
     __shared__ int s_ticket;
+    uint32_t(*s_whist)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_kw);
+    uint32_t *s_k = s_kw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = 1 << a.digit_bits;  // digits of this sort: 2 .. kMaxRadix
     if (tid == 0) s_ticket = (int)atomicAdd(&a.tickets[pass], 1u);
-    for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
+    for (int k = tid; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
     __syncthreads();
     const int t = s_ticket;
     const uint32_t total = *a.total;
     const uint32_t used = (total + kSortTile - 1) / kSortTile;
     if ((uint32_t)t >= used) return;
-    const int shift = pass * kRadixBits;
+    const int shift = pass * a.digit_bits;
+    const uint32_t dmask = (uint32_t)(R - 1);
     const uint32_t *kin = a.keys[src], *vin = a.vals[src];
     uint32_t *kout = a.keys[src ^ 1], *vout = a.vals[src ^ 1];
+    constexpr int kPerMax = kMaxRadix / kSortThreads;
+    const int per = (R + kSortThreads - 1) / kSortThreads;
 
-    // Global digit offsets: exclusive scan of this pass's histogram.
-    {
-        const uint32_t v = a.ghist[pass * kRadix + tid];
-        uint32_t incl = v;
+    // Exclusive scan of in[0, R) into out[0, R); thread tid owns digits
+    // [tid * per, tid * per + per). Block-wide (uses s_wsum).
+    auto block_scan = [&](const uint32_t *in, uint32_t *out) {
+        const int d0 = tid * per;
+        uint32_t v[kPerMax], loc = 0;
+#pragma unroll
+        for (int i = 0; i < kPerMax; ++i) {
+            v[i] = (i < per && d0 + i < R) ? in[d0 + i] : 0u;
+            loc += v[i];
+        }
+        uint32_t incl = loc;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t x = __shfl_up_sync(kFull, incl, o);
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += x;
         }
         if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
-        uint32_t off = 0;
+        uint32_t off = incl - loc;
         for (int w = 0; w < warp; ++w) off += s_wsum[w];
-        s_scan[tid] = off + incl - v;
-    }
+#pragma unroll
+        for (int i = 0; i < kPerMax; ++i) {
+            if (i < per && d0 + i < R) out[d0 + i] = off;
+            off += v[i];
+        }
+        __syncthreads();
+    };
+    block_scan(a.ghist + pass * kMaxRadix, s_scan);
 
     // Stable per-warp ranking: item order is (warp, iteration, lane).
     const uint32_t wbase = (uint32_t)t * kSortTile + (uint32_t)warp * 32 * kSortItems;
@@ -232,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
         const uint32_t vmask = __ballot_sync(kFull, valid);
         uint32_t r = 0;
         if (valid) {
-            const uint32_t d = (key[it] >> shift) & (kRadix - 1);
+            const uint32_t d = (key[it] >> shift) & dmask;
             const uint32_t peers = __match_any_sync(vmask, d);
             const uint32_t below = peers & lanemask_lt();
             const uint32_t prev = s_whist[warp][d];
@@ -246,24 +275,24 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
     __syncthreads();
 
     // Per digit: prefix over warps, block count, decoupled look-back.
-    {
-        const int d = tid;
+    for (int d = tid; d < R; d += kSortThreads) {
         uint32_t run = 0;
         for (int w = 0; w < kSortWarps; ++w) {
             const uint32_t c = s_whist[w][d];
             s_whist[w][d] = run;
             run += c;
         }
-        unsigned long long *lb = a.lookback + ((size_t)pass * a.n_sort_blocks) * kRadix;
+        s_cnt[d] = run;
+        unsigned long long *lb = a.lookback + ((size_t)pass * a.n_sort_blocks) * R;
         unsigned long long excl = 0;
         if (t == 0) {
             st_relaxed(&lb[d], kFlagInc | run);
         } else {
-            st_relaxed(&lb[(size_t)t * kRadix + d], kFlagAgg | run);
+            st_relaxed(&lb[(size_t)t * R + d], kFlagAgg | run);
             int pred = t - 1;
             uint32_t spins = 0;
             while (pred >= 0) {
-                const unsigned long long v = ld_relaxed(&lb[(size_t)pred * kRadix + d]);
+                const unsigned long long v = ld_relaxed(&lb[(size_t)pred * R + d]);
                 const unsigned long long flag = v & ~kCountMask;
                 if (flag == 0) {
                     if (++spins > kSpinLimit) {
@@ -277,22 +306,40 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
                 if (flag == kFlagInc) break;
                 --pred;
             }
-            st_relaxed(&lb[(size_t)t * kRadix + d], kFlagInc | ((excl + run) & kCountMask));
+            st_relaxed(&lb[(size_t)t * R + d], kFlagInc | ((excl + run) & kCountMask));
         }
         s_base[d] = s_scan[d] + (uint32_t)excl;
     }
     __syncthreads();
+    block_scan(s_cnt, s_bstart);
 
+    // Block-local positions in digit order, then the keys and values are
+    // placed there (s_k reuses the per-warp counters' storage) and written
+    // out in runs of equal digits, so consecutive threads store to
+    // consecutive addresses.
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t d = (key[it] >> shift) & dmask;
+        rank[it] += s_bstart[d] + s_whist[warp][d];
+    }
+    __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const uint32_t idx = wbase + it * 32 + lane;
-        if (idx < total) {
-            const uint32_t d = (key[it] >> shift) & (kRadix - 1);
-            const uint32_t pos = s_base[d] + s_whist[warp][d] + rank[it];
-            if (pos < total) {  // always true unless a bounded wait gave up
-                kout[pos] = key[it];
-                vout[pos] = val[it];
-            }
+        if (idx < total && rank[it] < (uint32_t)kSortTile) {
+            s_k[rank[it]] = key[it];
+            s_v[rank[it]] = val[it];
+        }
+    }
+    __syncthreads();
+    const uint32_t n_here = min((uint32_t)kSortTile, total - (uint32_t)t * kSortTile);
+    for (uint32_t i = tid; i < n_here; i += kSortThreads) {
+        const uint32_t k = s_k[i];
+        const uint32_t d = (k >> shift) & dmask;
+        const uint32_t pos = s_base[d] + (i - s_bstart[d]);
+        if (pos < total) {  // always true unless a bounded wait gave up
+            kout[pos] = k;
+            vout[pos] = s_v[i];
         }
     }
 }

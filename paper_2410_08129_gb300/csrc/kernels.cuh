@@ -16,8 +16,8 @@ constexpr int kPreThreads = 256;     // preprocess / emit block size
 constexpr int kSortThreads = 256;    // onesweep block size
 constexpr int kSortItems = 16;       // keys per thread per onesweep block
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxRadixBits = 9;     // widest digit: keys of up to 18 bits sort in two passes
+constexpr int kMaxRadix = 1 << kMaxRadixBits;
 constexpr int kMaxPasses = 4;
 constexpr int kMaxViews = HTGS_MAX_VIEWS;
 
@@ -108,9 +108,10 @@ struct SortArgs {
     int64_t capacity;
     const uint32_t *total;
     int passes;
+    int digit_bits;        // bits per pass (every pass the same), at most kMaxRadixBits
     uint32_t *keys[2], *vals[2];
-    uint32_t *ghist;       // kMaxPasses * kRadix
-    unsigned long long *lookback;  // passes * n_sort_blocks * kRadix flag|count words
+    uint32_t *ghist;       // kMaxPasses * kMaxRadix
+    unsigned long long *lookback;  // passes * n_sort_blocks * 2^digit_bits flag|count words
     uint32_t *tickets;     // kMaxPasses
     int n_sort_blocks;
     int *status;
@@ -184,7 +185,7 @@ __global__ void preprocess_backward_kernel(const __grid_constant__ Batch b, PreB
 // Binning: scan of per-block sums, then emit (global tile, record) instances.
 void launch_scan_blocks(const BinArgs &a, cudaStream_t s);
 void launch_emit(const Batch &b, const BinArgs &a, cudaStream_t s);
-// Stable LSD radix sort of (key, value) pairs by the low `passes * 8` bits.
+// Stable LSD radix sort of (key, value) pairs by the low passes * digit_bits bits.
 // Returns the buffer index (0 or 1) holding the result.
 int launch_sort(const SortArgs &a, cudaStream_t s);
 void launch_ranges(RangeArgs a, cudaStream_t s);

@@ -125,3 +125,43 @@ def test_batch_captured_in_cuda_graph():
     assert st == B.HTGS_OK
     for a, b in zip(eager, br.images):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n_views,size,tile", [(1, (3840, 2160), (8, 8)), (3, (3840, 2160), (8, 8)),
+                                               (2, (64, 48), (16, 16))])
+def test_sorted_tile_lists(n_views, size, tile):
+    """The radix sort splits the tile-key bits evenly into the fewest passes
+    of at most 9 bits: 129,600 tiles of one 4K view at 8x8 take 2 passes of
+    9 bits, three such views (388,800 tiles) 3 passes of 7 bits, 24 tiles one
+    pass. Sorted keys are non-decreasing, each tile's records ascending (a
+    stable sort of the gid-ordered emission) and the ranges delimit them."""
+    scene = _scene(3000, 7)
+    g = GaussianTensors.from_scene(scene)
+    cams = [scenes.fov_camera(scenes.look_at((0.3 * i, 0.0, 0.0), (0.0, 0.0, 3.0)), size[0], size[1], 60.0).rounded()
+            for i in range(n_views)]
+    prm = scenes.Params(K=4)
+    br = BatchRenderer([g] * n_views, cams, prm, launch=B.c_launch(tile, 1))
+    br.forward()
+    torch.cuda.synchronize()
+    lay = B.htgs_batch_workspace_layout(br.views(), prm, br.launch, br.capacity)
+    total = int(br.last_instances)
+    ws = br.workspace
+    keys = ws[lay.sorted_keys: lay.sorted_keys + 4 * total].view(torch.int32).cpu().numpy().astype(np.int64)
+    vals = ws[lay.sorted_vals: lay.sorted_vals + 4 * total].view(torch.int32).cpu().numpy().astype(np.int64)
+    ranges = ws[lay.ranges: lay.ranges + 8 * lay.n_tiles].view(torch.int32).view(-1, 2).cpu().numpy()
+    assert total > 0 and keys.min() >= 0 and keys.max() < lay.n_tiles
+    assert np.all(np.diff(keys) >= 0)
+    same = np.diff(keys) == 0
+    assert np.all(np.diff(vals)[same] > 0)
+    starts = np.flatnonzero(np.r_[True, ~same])
+    ends = np.r_[starts[1:], total]
+    np.testing.assert_array_equal(ranges[keys[starts], 0], starts)
+    np.testing.assert_array_equal(ranges[keys[starts], 1], ends)
+    # every record of a view appears at most once per tile and belongs to the tile's view
+    tiles_per_view = [((c.width + tile[0] - 1) // tile[0]) * ((c.height + tile[1] - 1) // tile[1]) for c in cams]
+    view_of_key = np.searchsorted(np.cumsum(tiles_per_view), keys, side="right")
+    np.testing.assert_array_equal(vals // scene.n, view_of_key)
+    for k, (cam, img) in enumerate(zip(cams, br.images)):
+        r = Renderer(cam, prm, scene.n, launch=B.c_launch(tile, 1))
+        ref = r.forward(g)
+        assert float((img - ref).abs().max()) <= 1e-5
