@@ -52,6 +52,36 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, int deg, floa
     Y[15] = -kSH3a * x * (xx - 3.f * yy);
 }
 
+// Colour of one Gaussian before the clamp: 0.5 + sum_k Y_k(dir) sh_k for
+// degree DEG (compile time, so Y stays in registers). Rows whose length
+// (3 (DEG+1)^2 floats) is a multiple of 4 are read as float4.
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const float *__restrict__ sh, float x, float y, float z,
+                                          float rgb[3]) {
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    float Y[16];
+    sh_eval(x, y, z, DEG, Y);
+    float c[3 * NC];
+    if constexpr ((3 * NC) % 4 == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(sh);
+#pragma unroll
+        for (int j = 0; j < 3 * NC / 4; ++j) {
+            const float4 v = __ldg(s4 + j);
+            c[4 * j] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3 * NC; ++j) c[j] = __ldg(sh + j);
+    }
+    rgb[0] = rgb[1] = rgb[2] = 0.5f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        rgb[0] += Y[k] * c[3 * k + 0];
+        rgb[1] += Y[k] * c[3 * k + 1];
+        rgb[2] += Y[k] * c[3 * k + 2];
+    }
+}
+
 // d(sum_k w_k Y_k)/d(x, y, z) for a weight vector w.
 __device__ __forceinline__ void sh_grad(float x, float y, float z, int deg, const float w[16],
                                         float g[3]) {
@@ -194,6 +224,7 @@ __device__ __forceinline__ void make_expansion(const Setup &S, const CamArgs &ca
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
+    __shared__ float4 s_recs[kPreThreads / 32][32 * kRecF4];
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     uint32_t count = 0;
     unsigned long long box_pixels = 0;
@@ -274,14 +305,13 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
                 for (int k = 0; k < 6; ++k) q[k] = hl * (rc * d[k] - n[k]);
                 // Colour (Sec. 3.1, identical to 3DGS): max(0, 0.5 + sum Y_k sh_k).
                 const int nc = (V.sh_degree + 1) * (V.sh_degree + 1);
-                float Y[16];
-                sh_eval(S.dir[0], S.dir[1], S.dir[2], V.sh_degree, Y);
                 const float *sh = V.sh + g * nc * 3;
-                float rgb[3] = {0.5f, 0.5f, 0.5f};
-                for (int k = 0; k < nc; ++k) {
-                    rgb[0] += Y[k] * sh[3 * k + 0];
-                    rgb[1] += Y[k] * sh[3 * k + 1];
-                    rgb[2] += Y[k] * sh[3 * k + 2];
+                float rgb[3];
+                switch (V.sh_degree) {
+                case 0: sh_colour<0>(sh, S.dir[0], S.dir[1], S.dir[2], rgb); break;
+                case 1: sh_colour<1>(sh, S.dir[0], S.dir[1], S.dir[2], rgb); break;
+                case 2: sh_colour<2>(sh, S.dir[0], S.dir[1], S.dir[2], rgb); break;
+                default: sh_colour<3>(sh, S.dir[0], S.dir[1], S.dir[2], rgb); break;
                 }
                 rec[0] = make_float4(q[0], d[0], q[1], d[1]);
                 rec[1] = make_float4(q[2], d[2], q[3], d[3]);
@@ -297,10 +327,28 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
                 rec[7] = make_float4(zlo, 0.f, 0.f, 0.f);
             }
         }
-        float4 *dst = a.rec + i * kRecF4;
-        for (int k = 0; k < kRecF4; ++k) dst[k] = rec[k];
+        // Stage the record in the warp's shared-memory slab (float4 slots
+        // XOR-swizzled by the lane so that neither side has bank conflicts).
+        const int lane = threadIdx.x & 31;
+        float4 *slab = s_recs[threadIdx.x >> 5];
+#pragma unroll
+        for (int k = 0; k < kRecF4; ++k) slab[lane * kRecF4 + (k ^ (lane & 7))] = rec[k];
         a.rect[i] = rect;
         a.count[i] = count;
+    }
+    // The warp's 32 records are contiguous in global memory: store them as
+    // 4 KB of consecutive float4s.
+    {
+        const int lane = threadIdx.x & 31;
+        const int64_t w0 = (int64_t)blockIdx.x * kPreThreads + (threadIdx.x & ~31);
+        const float4 *slab = s_recs[threadIdx.x >> 5];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < kRecF4; ++k) {
+            const int idx = k * 32 + lane;    // float4 index inside the warp's 32 records
+            const int r = idx / kRecF4, f = idx % kRecF4;
+            if (w0 + r < b.n_rec) a.rec[w0 * kRecF4 + idx] = slab[r * kRecF4 + (f ^ (r & 7))];
+        }
     }
     // Block sum of counts for the instance scan.
     __shared__ uint32_t warp_sums[kPreThreads / 32];
