@@ -422,6 +422,8 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     __shared__ uint32_t s_wgid[NW][2];
     __shared__ uint32_t s_next;
     __shared__ int s_item;
+    __shared__ float s_wzmax[NW];
+    __shared__ int s_wopen[NW];
     const int K = a.prm.K;
     const int n_items = min((int)*a.n_items, a.max_items);
     float4 *s_pa = smem;                 // g.xyz, k0
@@ -459,7 +461,11 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     const size_t npix = (size_t)width * height;
     const uint2 range = chunk_range(a.ranges[tile], work.y, work.z);
 
-    // Phase A: per-pixel adjoint state.
+    // Phase A: per-pixel adjoint state. Also, over the tile's pixels: the
+    // deepest last core entry of full cores and whether a core is not full
+    // (there every candidate belongs to it).
+    float zmax_l = -INFINITY;
+    bool open_l = false;
     for (int p = tid; p < TP; p += kBwdThreads) {
         const int x = x0 + p % TW, y = y0 + p / TW;
         const bool inside = x < width && y < height;
@@ -528,9 +534,26 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
         // mode 0: no core (K = 0); 1: every candidate is in the core; 2: compare with the last entry.
         const int mode = K == 0 ? 0 : (n_core < K ? 1 : 2);
         s_pc[p] = make_float4(lastz, __uint_as_float(lastg), __int_as_float(mode), 0.f);
+        if (inside && mode == 1) open_l = true;
+        if (inside && mode == 2) zmax_l = fmaxf(zmax_l, lastz);
+    }
+    for (int o = 16; o > 0; o >>= 1) zmax_l = fmaxf(zmax_l, __shfl_xor_sync(0xffffffffu, zmax_l, o));
+    open_l = __any_sync(0xffffffffu, open_l);
+    if (lane == 0) {
+        s_wzmax[warp] = zmax_l;
+        s_wopen[warp] = open_l ? 1 : 0;
     }
     if (tid == 0) s_next = range.x;
     __syncthreads();
+    // A record whose depths all exceed the deepest last core entry belongs
+    // to no pixel's core in this tile (unless some core is not full).
+    float tile_zmax = -INFINITY;
+    int tile_open = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        tile_zmax = fmaxf(tile_zmax, s_wzmax[w]);
+        tile_open |= s_wopen[w];
+    }
 
     // Phase B: warps pull records; lanes walk the record's box in the tile.
     auto grab = [&]() -> uint32_t {
@@ -546,7 +569,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
         }
         cp_async_commit();
     };
-    constexpr float kTwoLn2 = 1.3862943611198906f;
+    constexpr float kLn2 = 0.69314718055994531f;
     uint32_t j = grab();
     int slot = 0;
     if (j < range.y) issue(j, 0);
@@ -569,6 +592,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
         if (ix0 <= ix1 && iy0 <= iy1) {
             const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c3 = rec[3], c4 = rec[4], c5 = rec[5];
             const float zlo = rec[7].x;
+            const bool may_core = tile_open || !(zlo > tile_zmax);
             float2 acc[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -588,7 +612,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                     const int p = prow + x;
                     const float al = f.alpha;
                     bool in_core = false;
-                    if (al >= tau_K) {
+                    if (may_core && al >= tau_K) {
                         const float4 PC = s_pc[p];
                         const int mode = __float_as_int(PC.z);
                         if (mode == 1) {
@@ -622,19 +646,24 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                     touched = true;
                     gc0 += dc0; gc1 += dc1; gc2 += dc2;
                     if (f.araw < alpha_max) {
-                        gaa += dA * al;
-                        // rho^2 = N / D: dL/dN = dL/drho^2 / D, dL/dD = -dL/dN rho^2.
-                        const float drho2 = -0.5f * al * dA;
-                        const float rho2 = c5.w - kTwoLn2 * f.t;
-                        const float dN = drho2 * f.rD;
-                        const float2 nd = make_float2(dN, -dN * rho2);
+                        // With g = alpha dL/dalpha: dL/drho^2 = -g/2, and as
+                        // rho^2 = N / D = rho_c - 2 ln2 t, dL/dN = -e/2 and
+                        // dL/dD = e rho^2 / 2 = (rho_c e - 2 ln2 e t) / 2 for
+                        // e = g / D. The pixel adds the moments of (e, e t);
+                        // the (record, tile) sums become dL/dN and dL/dD once,
+                        // after the warp reduction.
+                        const float g = dA * al;
+                        gaa += g;
+                        const float e = g * f.rD;
+                        const float2 et = make_float2(e, e * f.t);
                         const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
-                        acc[0].x += nd.x; acc[0].y += nd.y;
-                        acc[1] = ffma2(nd, X, acc[1]);
-                        acc[2] = ffma2(nd, Y, acc[2]);
-                        acc[3] = ffma2(nd, fmul2(X, X), acc[3]);
-                        acc[4] = ffma2(nd, fmul2(X, Y), acc[4]);
-                        acc[5] = ffma2(nd, fmul2(Y, Y), acc[5]);
+                        const float2 ex = fmul2(et, X), ey = fmul2(et, Y);
+                        acc[0] = fadd2(acc[0], et);
+                        acc[1] = fadd2(acc[1], ex);
+                        acc[2] = fadd2(acc[2], ey);
+                        acc[3] = ffma2(ex, X, acc[3]);
+                        acc[4] = ffma2(ex, Y, acc[4]);
+                        acc[5] = ffma2(ey, Y, acc[5]);
                     }
                 }
             }
@@ -642,8 +671,15 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                 float v[16] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y,
                                acc[4].x, acc[4].y, acc[5].x, acc[5].y, gaa, gc0, gc1, gc2};
                 warp_reduce16_to4(v, lane);
-                if ((lane & 7) == 0)
+                if ((lane & 7) == 0) {
+                    if (lane < 24) {  // two (sum e m, sum e t m) pairs -> (dL/dN_m, dL/dD_m)
+                        const float rc = c5.w;
+                        const float n0 = -0.5f * v[0], d0 = 0.5f * rc * v[0] - kLn2 * v[1];
+                        const float n1 = -0.5f * v[2], d1 = 0.5f * rc * v[2] - kLn2 * v[3];
+                        v[0] = n0; v[1] = d0; v[2] = n1; v[3] = d1;
+                    }
                     red_add_v4(a.acc + (size_t)gid * 16 + (lane >> 3) * 4, v[0], v[1], v[2], v[3]);
+                }
             }
         }
         __syncwarp();
