@@ -58,7 +58,8 @@ def build(force: bool = False) -> str:
 class _Gaussians(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("logits", ctypes.c_void_p),
-                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32)]
+                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
+                ("filter_var", ctypes.c_void_p)]
 
 
 class _Camera(ctypes.Structure):
@@ -86,7 +87,8 @@ class _Splat(ctypes.Structure):
                 ("p", ctypes.c_double * 2), ("h", ctypes.c_double * 2),
                 ("rect", ctypes.c_int32 * 4),
                 ("dir", ctypes.c_double * 3), ("dist", ctypes.c_double),
-                ("rgb_raw", ctypes.c_double * 3), ("rgb", ctypes.c_double * 3)]
+                ("rgb_raw", ctypes.c_double * 3), ("rgb", ctypes.c_double * 3),
+                ("o_raw", ctypes.c_double), ("s_raw", ctypes.c_double * 3), ("filter_var", ctypes.c_double)]
 
 
 class _Diag(ctypes.Structure):
@@ -148,9 +150,12 @@ class _Keep:
         self.quats = _f64(scene.quats)
         self.logits = _f64(scene.opacity_logits)
         self.sh = _f64(scene.sh)
+        fv = getattr(scene, "filter_var", None)
+        self.filter_var = _f64(fv) if fv is not None else None
         self.g = _Gaussians(self.means.ctypes.data, self.log_scales.ctypes.data,
                             self.quats.ctypes.data, self.logits.ctypes.data, self.sh.ctypes.data,
-                            self.means.shape[0], int(scene.sh_degree))
+                            self.means.shape[0], int(scene.sh_degree),
+                            self.filter_var.ctypes.data if self.filter_var is not None else None)
 
 
 def _camera(cam) -> _Camera:
@@ -185,7 +190,8 @@ SPLAT_DTYPE = np.dtype([("valid", np.int32), ("cull_reason", np.int32), ("cull_m
                         ("r1", np.float64, 4), ("r2", np.float64, 4), ("r4", np.float64, 4),
                         ("p", np.float64, 2), ("h", np.float64, 2), ("rect", np.int32, 4),
                         ("dir", np.float64, 3), ("dist", np.float64),
-                        ("rgb_raw", np.float64, 3), ("rgb", np.float64, 3)], align=True)
+                        ("rgb_raw", np.float64, 3), ("rgb", np.float64, 3), ("o_raw", np.float64),
+                        ("s_raw", np.float64, 3), ("filter_var", np.float64)], align=True)
 
 
 def preprocess(scene, cam, params) -> np.ndarray:

@@ -49,6 +49,7 @@ typedef struct {
     const double *sh;         /* N x (deg+1)^2 x 3 */
     int64_t n;
     int32_t sh_degree;
+    const double *filter_var; /* N or NULL: variance of the 3D smoothing filter */
 } og_gaussians;
 
 typedef struct {
@@ -84,6 +85,9 @@ typedef struct {
     double dist;         /* |mean - camera centre| */
     double rgb_raw[3];   /* 0.5 + SH sum, before the clamp */
     double rgb[3];       /* colour */
+    double o_raw;        /* sigmoid(logit) before the 3D filter (o = o_raw without one) */
+    double s_raw[3];     /* exp(log-scales) before the 3D filter */
+    double filter_var;   /* the 3D filter's variance (0 without one) */
 } og_splat;
 
 /* Optional per-pixel diagnostics of og_render (each pointer may be NULL). */
@@ -267,6 +271,20 @@ static void og_setup_one(const og_gaussians *g, const og_camera *cam, const og_p
     /* Sec. 3.1: sigmoid opacity, log-space scales, normalised quaternion. */
     out->o = 1.0 / (1.0 + exp(-g->logits[i]));
     for (int k = 0; k < 3; ++k) out->s[k] = exp(g->log_scales[3 * i + k]);
+    /* 3D smoothing filter (Sec. 4.2, after Yu et al.): the Gaussian is
+       convolved with an isotropic Gaussian of variance v, Sigma + v I =
+       R diag(s^2 + v) R^T, and its opacity is scaled by
+       sqrt(det Sigma / det (Sigma + v I)) so that its integral is kept. */
+    out->o_raw = out->o;
+    for (int k = 0; k < 3; ++k) out->s_raw[k] = out->s[k];
+    out->filter_var = g->filter_var ? g->filter_var[i] : 0.0;
+    if (g->filter_var) {
+        for (int k = 0; k < 3; ++k) {
+            const double sf = sqrt(out->s_raw[k] * out->s_raw[k] + out->filter_var);
+            out->o *= out->s_raw[k] / sf;
+            out->s[k] = sf;
+        }
+    }
     const double *qr = g->quats + 4 * i;
     double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
     for (int k = 0; k < 4; ++k) out->q[k] = qr[k] / qn;
@@ -971,7 +989,11 @@ static void og_chain_task(void *vctx, int64_t b, int64_t e) {
                 ds += sp->R[k][j] * dT[k][j];
                 dR[k][j] = sp->s[j] * dT[k][j];
             }
-            dls[j] = ds * sp->s[j]; /* s = exp(log s) */
+            /* s = exp(log s); with the 3D filter s' = sqrt(s^2 + v) and
+               o' = o prod_k s_k / s'_k, so d s'_j / d log s_j = s_j^2 / s'_j
+               and d o' / d log s_j = o' v / s'_j^2 (rg[12] = dL/do'). */
+            dls[j] = ds * sp->s_raw[j] * sp->s_raw[j] / sp->s[j] +
+                     rg[12] * sp->o * sp->filter_var / (sp->s[j] * sp->s[j]);
         }
         /* R(q) of the unit quaternion q = (w, x, y, z). */
         const double w = sp->q[0], x = sp->q[1], y = sp->q[2], z = sp->q[3];
@@ -988,8 +1010,8 @@ static void og_chain_task(void *vctx, int64_t b, int64_t e) {
         double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
         double dot = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
         for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - sp->q[k] * dot) / qn;
-        /* o = sigmoid(logit). */
-        c->d_logits[i] = rg[12] * sp->o * (1.0 - sp->o);
+        /* o' = o prod_k s_k / s'_k with o = sigmoid(logit): d o'/d logit = o' (1 - o). */
+        c->d_logits[i] = rg[12] * sp->o * (1.0 - sp->o_raw);
         /* colour = max(0, 0.5 + sum_k Y_k(dir) k_k); dir = (mu - centre)/|mu - centre|. */
         double Y[16], dY[16][3];
         og_sh_basis(sp->dir, c->gs->sh_degree, Y, dY);

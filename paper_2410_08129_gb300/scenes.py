@@ -34,29 +34,39 @@ class Scene:
     opacity_logits: np.ndarray  # (N,) float32
     sh: np.ndarray             # (N, (deg+1)^2, 3) float32
     sh_degree: int
+    filter_var: np.ndarray | None = None  # (N,) float32: 3D smoothing-filter variance, or None
 
     @property
     def n(self) -> int:
         return int(self.means.shape[0])
 
+    def _fv(self, f):
+        return None if self.filter_var is None else f(self.filter_var)
+
     def astype(self, dtype) -> "Scene":
         return Scene(self.means.astype(dtype), self.log_scales.astype(dtype),
                      self.quats.astype(dtype), self.opacity_logits.astype(dtype),
-                     self.sh.astype(dtype), self.sh_degree)
+                     self.sh.astype(dtype), self.sh_degree, self._fv(lambda v: v.astype(dtype)))
 
     def subset(self, idx) -> "Scene":
         idx = np.asarray(idx)
         return Scene(self.means[idx].copy(), self.log_scales[idx].copy(),
                      self.quats[idx].copy(), self.opacity_logits[idx].copy(),
-                     self.sh[idx].copy(), self.sh_degree)
+                     self.sh[idx].copy(), self.sh_degree, self._fv(lambda v: v[idx].copy()))
 
     def concat(self, other: "Scene") -> "Scene":
         assert other.sh_degree == self.sh_degree
+        assert (self.filter_var is None) == (other.filter_var is None)
         return Scene(np.concatenate([self.means, other.means]),
                      np.concatenate([self.log_scales, other.log_scales]),
                      np.concatenate([self.quats, other.quats]),
                      np.concatenate([self.opacity_logits, other.opacity_logits]),
-                     np.concatenate([self.sh, other.sh]), self.sh_degree)
+                     np.concatenate([self.sh, other.sh]), self.sh_degree,
+                     self._fv(lambda v: np.concatenate([v, other.filter_var])))
+
+    def with_filter(self, filter_var) -> "Scene":
+        """The same Gaussians with a per-Gaussian 3D smoothing-filter variance."""
+        return dataclasses.replace(self, filter_var=np.asarray(filter_var, dtype=self.means.dtype).reshape(-1))
 
 
 @dataclasses.dataclass
