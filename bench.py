@@ -507,6 +507,29 @@ def main():
     ms_per_step = total_ms / args.steps
     fps = job_throughput(args.steps, world, total_ms)
 
+    # ---- the same frame with the 3D smoothing filter (Sec. 4.2) -----------
+    fscene = scene.with_filter(scenes.filter_variance_from_cameras(scene.means, [cam]))
+    fg = GaussianTensors.from_scene(fscene)
+    fr = Renderer(cam, prm, scene.n, launch=B.c_launch((16, 16), 1))
+    fimg = fr.image_buffer()
+    fr.forward(fg, image=fimg, save=False, check=True)
+    for _ in range(max(args.warmup, 3)):
+        fr.forward(fg, image=fimg, save=False, check=False)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        fr.forward(fg, image=fimg, save=False, check=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    st3, finst = fr.status()
+    assert st3 == B.HTGS_OK
+    filter_ms = max_over_ranks(f0.elapsed_time(f1))
+    filtered = {"value": job_throughput(args.steps, world, filter_ms), "unit": UNIT,
+                "ms_per_step": filter_ms / args.steps, "instances": finst,
+                "workload": "the headline frame with the 3D filter, variance (0.2 depth / focal)^2 per Gaussian"}
+    del fr, fg, fimg
+
     # ---- end to end through the C ABI with host buffers --------------------
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
@@ -615,6 +638,7 @@ def main():
                     "workload": "500k Gaussians (box distribution), 1200x800, K=8: render + L1 + backward",
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
                     "grads_finite": gfinite},
+        "filter3d": filtered,
         "batched_vs_plain": batched,
         "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,

@@ -61,6 +61,11 @@ typedef struct {
     const float *sh;
     int64_t n;
     int32_t sh_degree;
+    /* NULL, or n floats: the variance v of the 3D smoothing filter applied to
+     * each Gaussian before rendering (Sec. 4.2, the 3D filter of Yu et al.):
+     * scales become sqrt(s^2 + v) and the opacity is scaled by
+     * prod s / sqrt(s^2 + v); v is an input, no gradient flows to it. */
+    const float *filter_var;
 } htgs_gaussians;
 
 /* Gradient outputs, same shapes as htgs_gaussians. Device pointers. */

@@ -31,7 +31,8 @@ HTGS_MAX_CAPACITY = (1 << 31) - 1
 class Gaussians(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
-                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32)]
+                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
+                ("filter_var", ctypes.c_void_p)]
 
 
 class GaussiansGrad(ctypes.Structure):
@@ -156,12 +157,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
 
 
-def c_gaussians(means, log_scales, quats, logits, sh, sh_degree) -> Gaussians:
-    for t in (means, log_scales, quats, logits, sh):
+def c_gaussians(means, log_scales, quats, logits, sh, sh_degree, filter_var=None) -> Gaussians:
+    for t in (means, log_scales, quats, logits, sh) + ((filter_var,) if filter_var is not None else ()):
         if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
             raise ValueError("Gaussian parameters must be contiguous float32 CUDA tensors")
+    if filter_var is not None and filter_var.numel() != means.shape[0]:
+        raise ValueError("filter_var needs one variance per Gaussian")
     return Gaussians(_ptr(means).value, _ptr(log_scales).value, _ptr(quats).value, _ptr(logits).value,
-                     _ptr(sh).value, int(means.shape[0]), int(sh_degree))
+                     _ptr(sh).value, int(means.shape[0]), int(sh_degree),
+                     _ptr(filter_var).value if filter_var is not None else None)
 
 
 def _stream(stream=None):

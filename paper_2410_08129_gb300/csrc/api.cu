@@ -194,7 +194,7 @@ void make_batch(int n_views, const htgs_view *views, const Layout &L, bool backw
         make_cam(&hv.camera, d.cam);
         const htgs_gaussians *g = hv.gaussians;
         d.means = g->means; d.log_scales = g->log_scales; d.quats = g->quats;
-        d.logits = g->opacity_logits; d.sh = g->sh;
+        d.logits = g->opacity_logits; d.sh = g->sh; d.filter_var = g->filter_var;
         d.n = g->n;
         d.sh_degree = g->sh_degree;
         d.rec_off = rec;

@@ -35,6 +35,7 @@ constexpr int kSchedBuckets = 64;
 struct ViewDesc {
     CamArgs cam;
     const float *means, *log_scales, *quats, *logits, *sh;
+    const float *filter_var;  // nullptr: no 3D filter
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
     float *image;          // H x W x 3
     float *saved;          // (7 + K) planes of H*W, or nullptr

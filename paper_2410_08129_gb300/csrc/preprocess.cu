@@ -140,8 +140,11 @@ __device__ __forceinline__ V3 cross(V3 a, V3 b) {
 // Geometry shared by the forward and the backward setup.
 struct Setup {
     bool valid;
-    float o, rho_c;
-    float s[3];
+    float o, rho_c;    // opacity and cutoff of the rendered (filtered) Gaussian
+    float o_raw;       // sigmoid(logit)
+    float s[3];        // scales of the rendered Gaussian
+    float s_raw[3];    // exp(log-scales)
+    float fvar;        // 3D filter variance (0 without a filter)
     float q[4];        // normalised (w, x, y, z)
     float qnorm;
     float R[3][3];
@@ -154,15 +157,29 @@ struct Setup {
 __device__ __forceinline__ void setup_geometry(const float *__restrict__ means,
                                                const float *__restrict__ log_scales,
                                                const float *__restrict__ quats,
-                                               const float *__restrict__ logits, int64_t i,
+                                               const float *__restrict__ logits,
+                                               const float *__restrict__ filter_var, int64_t i,
                                                const CamArgs &cam, const ParamArgs &prm,
                                                Setup &S) {
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
     const float l = logits[i];
     // o = sigmoid(logit); rho_c = 2 ln(o / tau_alpha) = -2 (ln(1 + e^{-l}) + ln tau_alpha).
     S.o = 1.f / (1.f + __expf(-l));
+    S.o_raw = S.o;
     S.rho_c = -2.f * (log1pf(__expf(-l)) + __logf(prm.tau_alpha));
-    for (int k = 0; k < 3; ++k) S.s[k] = __expf(log_scales[3 * i + k]);
+    for (int k = 0; k < 3; ++k) S.s[k] = S.s_raw[k] = __expf(log_scales[3 * i + k]);
+    // 3D smoothing filter (Sec. 4.2): convolution with an isotropic Gaussian
+    // of variance v. Scales become sqrt(s^2 + v) and the opacity is scaled by
+    // prod s / sqrt(s^2 + v), so rho_c drops by sum ln(1 + v / s^2).
+    S.fvar = filter_var ? filter_var[i] : 0.f;
+    if (filter_var) {
+        for (int k = 0; k < 3; ++k) {
+            const float r = S.fvar / (S.s_raw[k] * S.s_raw[k]);
+            S.s[k] = S.s_raw[k] * sqrtf(1.f + r);
+            S.o *= rsqrtf(1.f + r);
+            S.rho_c -= log1pf(r);
+        }
+    }
     const float4 qr = reinterpret_cast<const float4 *>(quats)[i];
     S.qnorm = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
     const float inv = 1.f / S.qnorm;
@@ -234,7 +251,7 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
         const int64_t g = i - V.rec_off;
         const CamArgs &cam = V.cam;
         Setup S;
-        setup_geometry(V.means, V.log_scales, V.quats, V.logits, g, cam, a.prm, S);
+        setup_geometry(V.means, V.log_scales, V.quats, V.logits, V.filter_var, g, cam, a.prm, S);
         uint2 rect = make_uint2(1u, 0u);
         float4 rec[kRecF4];
         for (int k = 0; k < kRecF4; ++k) rec[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -413,7 +430,7 @@ preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
         }
     };
     Setup S;
-    setup_geometry(V.means, V.log_scales, V.quats, V.logits, g, cam, a.prm, S);
+    setup_geometry(V.means, V.log_scales, V.quats, V.logits, V.filter_var, g, cam, a.prm, S);
     const uint2 rect = a.rect[i];
     const bool active = S.valid && ((rect.x & 0xffffu) <= (rect.x >> 16));
     if (!active) {
@@ -474,7 +491,10 @@ preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
             ds += dB[k][j] * S.R[k][j];
             dR[k][j] = dB[k][j] * S.s[j];
         }
-        gls[j] = ds * S.s[j];
+        // s' = sqrt(s^2 + v): d s'/d log s = s^2 / s'; and the filtered
+        // opacity o' = o prod s / s' has d o'/d log s = o' v / s'^2, with
+        // dL/do' = g_aa / o'.
+        gls[j] = ds * S.s_raw[j] * S.s_raw[j] / S.s[j] + A3.x * S.fvar / (S.s[j] * S.s[j]);
     }
     const float w = S.q[0], x = S.q[1], y = S.q[2], z = S.q[3];
     float dq[4];
@@ -488,8 +508,8 @@ preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
     const float pdot = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
     const float iq = 1.f / S.qnorm;
     for (int k = 0; k < 4; ++k) gq[k] = (dq[k] - S.q[k] * pdot) * iq;
-    // o = sigmoid(l): dL/dl = (sum dL/dalpha alpha / o) o (1 - o).
-    glogit = g_aa * (1.f - S.o);
+    // o' = sigmoid(l) prod s / s': dL/dl = (sum dL/dalpha alpha / o') o' (1 - sigmoid(l)).
+    glogit = g_aa * (1.f - S.o_raw);
     // Colour: channels clamped at zero pass no gradient.
     float Y[16];
     sh_eval(S.dir[0], S.dir[1], S.dir[2], V.sh_degree, Y);

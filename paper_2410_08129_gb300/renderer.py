@@ -30,6 +30,7 @@ class GaussianTensors:
     opacity_logits: torch.Tensor
     sh: torch.Tensor
     sh_degree: int
+    filter_var: torch.Tensor | None = None  # 3D smoothing-filter variance per Gaussian (not trained)
 
     @property
     def n(self) -> int:
@@ -39,12 +40,14 @@ class GaussianTensors:
     def from_scene(scene, device="cuda") -> "GaussianTensors":
         def t(a):
             return torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        fv = getattr(scene, "filter_var", None)
         return GaussianTensors(t(scene.means), t(scene.log_scales), t(scene.quats),
-                               t(scene.opacity_logits), t(scene.sh), int(scene.sh_degree))
+                               t(scene.opacity_logits), t(scene.sh), int(scene.sh_degree),
+                               t(fv) if fv is not None else None)
 
     def c_struct(self) -> B.Gaussians:
         return B.c_gaussians(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh,
-                             self.sh_degree)
+                             self.sh_degree, self.filter_var)
 
     def tensors(self):
         return [getattr(self, f) for f in FIELDS]
@@ -123,9 +126,9 @@ class RenderFunction(torch.autograd.Function):
     backward calls htgs_render_backward on the saved per-pixel state."""
 
     @staticmethod
-    def forward(ctx, renderer: Renderer, sh_degree: int, means, log_scales, quats, opacity_logits, sh):
+    def forward(ctx, renderer: Renderer, sh_degree: int, filter_var, means, log_scales, quats, opacity_logits, sh):
         g = GaussianTensors(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
-                            opacity_logits.contiguous(), sh.contiguous(), sh_degree)
+                            opacity_logits.contiguous(), sh.contiguous(), sh_degree, filter_var)
         image = renderer.forward(g, save=True, check=True)
         ctx.renderer = renderer
         ctx.g = g
@@ -134,12 +137,12 @@ class RenderFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dl_dimage):
         grads = ctx.renderer.backward(ctx.g, dl_dimage)
-        return (None, None) + tuple(grads[f] for f in FIELDS)
+        return (None, None, None) + tuple(grads[f] for f in FIELDS)
 
 
 def render(g: GaussianTensors, renderer: Renderer):
     """Differentiable render of one view (hybrid transparency, Eq. (15))."""
-    return RenderFunction.apply(renderer, g.sh_degree, g.means, g.log_scales, g.quats,
+    return RenderFunction.apply(renderer, g.sh_degree, g.filter_var, g.means, g.log_scales, g.quats,
                                 g.opacity_logits, g.sh)
 
 

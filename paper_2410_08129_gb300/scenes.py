@@ -248,6 +248,32 @@ def perturbed(scene: Scene, rng: np.random.Generator) -> Scene:
                  scene.sh.copy(), scene.sh_degree)
 
 
+def filter_variance_from_cameras(means, cameras, scale: float = 0.2, margin: float = 0.15) -> np.ndarray:
+    """Input recipe for the 3D smoothing filter (an input of the render, as a
+    training loop would compute it from its cameras): the filter's standard
+    deviation is `scale` times the smallest depth / focal length over the
+    cameras that see the mean (in front of the near plane, projecting into
+    the image widened by `margin` on each side); Gaussians seen by no camera
+    take the largest variance. Returns float32 variances."""
+    means = np.asarray(means, np.float64)
+    best = np.full(means.shape[0], np.inf)
+    for cam in cameras:
+        M = np.asarray(cam.world_to_cam, np.float64)
+        v = means @ M[:3, :3].T + M[:3, 3]
+        z = v[:, 2]
+        front = z > cam.z_near
+        zs = np.where(front, z, 1.0)
+        u = cam.fx * v[:, 0] / zs + cam.cx
+        w = cam.fy * v[:, 1] / zs + cam.cy
+        seen = front & (u >= -margin * cam.width) & (u <= (1 + margin) * cam.width) \
+            & (w >= -margin * cam.height) & (w <= (1 + margin) * cam.height)
+        best = np.where(seen, np.minimum(best, z / min(cam.fx, cam.fy)), best)
+    var = (scale * best) ** 2
+    seen_any = np.isfinite(var)
+    var[~seen_any] = var[seen_any].max() if seen_any.any() else 0.0
+    return var.astype(np.float32)
+
+
 def config4_views(n_views: int = 32, seed: int = 3):
     """32 cameras on a 6 m sphere around (0, 0, 3) looking at it; W ~ U{320..1600},
     H ~ U{240..1064} independently; 60 deg vertical FOV."""
