@@ -70,7 +70,7 @@ class _Camera(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("tau_alpha", ctypes.c_double), ("tau_K", ctypes.c_double),
-                ("alpha_max", ctypes.c_double), ("bg", ctypes.c_double * 3)]
+                ("alpha_max", ctypes.c_double), ("bg", ctypes.c_double * 3), ("no_tail", ctypes.c_int32)]
 
 
 class _Window(ctypes.Structure):
@@ -174,6 +174,7 @@ def _params(p) -> _Params:
     q.tau_alpha, q.tau_K, q.alpha_max = float(p.tau_alpha), float(p.tau_K), float(p.alpha_max)
     for i in range(3):
         q.bg[i] = float(p.bg[i])
+    q.no_tail = 1 if getattr(p, "no_tail", False) else 0
     return q
 
 

@@ -62,6 +62,7 @@ typedef struct {
     int32_t K;
     double tau_alpha, tau_K, alpha_max;
     double bg[3];
+    int32_t no_tail; /* 1: inference without the tail (Sec. 4.4): C = core + T_{K+1} bg */
 } og_params;
 
 typedef struct {
@@ -591,9 +592,9 @@ static void og_blend(og_fragvec *F, const og_params *prm, og_pixel_result *res) 
         T *= 1.0 - f->alpha;
     }
     res->T_core = T;
-    /* Tail: every other fragment, in any order. */
+    /* Tail: every other fragment, in any order (none when it is omitted). */
     double A = 0, S[3] = {0, 0, 0}, Tt = 1.0;
-    for (int64_t i = n_core; i < F->n; ++i) {
+    for (int64_t i = n_core; i < F->n && !prm->no_tail; ++i) {
         const og_frag *f = &F->f[i];
         A += f->alpha;
         for (int ch = 0; ch < 3; ++ch) S[ch] += f->alpha * f->c[ch];
@@ -891,6 +892,7 @@ static void og_bwd_gauss_task(void *vctx, int64_t b, int64_t e) {
                     break;
                 }
             }
+            if (!in_core && c->prm->no_tail) continue; /* an omitted tail has no gradient */
             if (!in_core) {
                 const double Tc = st->T_core, Tt = st->T_tail, A = st->A_tail;
                 for (int ch = 0; ch < 3; ++ch) {

@@ -100,6 +100,7 @@ class Params:
     tau_K: float = 0.05
     alpha_max: float = 0.999
     bg: tuple = (0.0, 0.0, 0.0)
+    no_tail: bool = False  # inference without the tail: core over the background
 
 
 def _unit_quats(rng: np.random.Generator, n: int) -> np.ndarray:

@@ -64,6 +64,16 @@ def test_analytic_gradient_matches_central_differences(K, tau_K):
     assert n_cmp > 0.8 * (n_cmp + n_skip) and n_cmp > 500
 
 
+@pytest.mark.parametrize("K", [2, 5])
+def test_no_tail_gradient_matches_central_differences(K):
+    scene = scenes.small_box_scene(14, seed=220 + K, sh_degree=1).astype(np.float64)
+    scene.log_scales += 0.7
+    cam = scenes.fov_camera(scenes.look_at((0.2, -0.1, -0.3), (0.0, 0.1, 3.0)), 40, 30, 60.0)
+    prm = scenes.Params(K=K, tau_K=0.05, bg=(0.3, 0.6, 0.2), no_tail=True)
+    n_cmp, n_skip = _fd_check(scene, cam, prm, (12, 8, 16, 14), seed=K)
+    assert n_cmp > 0.8 * (n_cmp + n_skip) and n_cmp > 300
+
+
 def test_gradient_zero_where_alpha_clamped_and_colour_clamped():
     """No gradient flows to the opacity where alpha = alpha_max, nor to SH
     coefficients of a channel clamped at zero."""

@@ -65,6 +65,27 @@ def test_k_at_least_fragments_is_sorted_alpha_blending(seed):
             assert d["T_core"][j, i] == pytest.approx(T, rel=1e-9, abs=1e-15)
 
 
+@pytest.mark.parametrize("K,tau_K", [(3, 0.05), (1, 0.1), (0, 0.05)])
+def test_no_tail_is_sorted_blend_of_the_core(K, tau_K):
+    """Inference without the tail (Sec. 4.4): the K nearest candidates
+    (alpha >= tau_K, (z, gid) order) blended over the background, and
+    nothing else contributes."""
+    scene = _scene(14, 50 + K)
+    cam = scenes.identity_camera(20, 16, 20.0)
+    prm = scenes.Params(K=K, tau_K=tau_K, bg=(0.7, 0.2, 0.4), no_tail=True)
+    img, d = oracle.render(scene, cam, prm, diagnostics=True)
+    deep = 0
+    for j in range(cam.height):
+        for i in range(cam.width):
+            fr = _independent_fragments(scene, cam, prm, i + 0.5, j + 0.5)
+            cand = sorted((f for f in fr if f[2] >= tau_K), key=lambda f: (f[0], f[1]))
+            ref, T = cf.sorted_alpha_blend(cand[:K], prm.bg)
+            np.testing.assert_allclose(img[j, i], ref, rtol=1e-9, atol=1e-12)
+            assert d["A_tail"][j, i] == 0.0 and d["T_tail"][j, i] == 1.0
+            deep += len(fr) > K
+    assert deep > 20  # pixels whose tail was dropped
+
+
 def test_k_zero_is_order_independent_blend():
     """K = 0 (full OIT): C = (1 - prod(1 - a)) sum(a c)/sum(a) + prod(1 - a) bg."""
     scene = _scene(14, 40)
