@@ -530,6 +530,27 @@ def main():
                 "workload": "the headline frame with the 3D filter, variance (0.2 depth / focal)^2 per Gaussian"}
     del fr, fg, fimg
 
+    # ---- the same frame rendered without the tail (inference variant) ------
+    nprm = scenes.Params(K=prm.K, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max,
+                         bg=prm.bg, no_tail=True)
+    nr = Renderer(cam, nprm, scene.n, launch=B.c_launch((16, 16), 1))
+    nimg = nr.image_buffer()
+    nr.forward(g, image=nimg, save=False, check=True)
+    for _ in range(max(args.warmup, 3)):
+        nr.forward(g, image=nimg, save=False, check=False)
+    torch.cuda.synchronize()
+    n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0.record(stream)
+    for _ in range(args.steps):
+        nr.forward(g, image=nimg, save=False, check=False)
+    n1.record(stream)
+    torch.cuda.synchronize()
+    assert nr.status()[0] == B.HTGS_OK
+    notail_ms = max_over_ranks(n0.elapsed_time(n1))
+    no_tail = {"value": job_throughput(args.steps, world, notail_ms), "unit": UNIT,
+               "ms_per_step": notail_ms / args.steps, "workload": "the headline frame without the tail"}
+    del nr, nimg
+
     # ---- end to end through the C ABI with host buffers --------------------
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
@@ -639,6 +660,7 @@ def main():
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
                     "grads_finite": gfinite},
         "filter3d": filtered,
+        "no_tail": no_tail,
         "batched_vs_plain": batched,
         "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,

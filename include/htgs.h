@@ -94,6 +94,8 @@ typedef struct {
     float tau_K;      /* minimum alpha for a fragment to enter the core */
     float alpha_max;  /* alpha = min(o e^{-rho^2/2}, alpha_max), alpha_max < 1 */
     float bg[3];      /* background colour c_bg */
+    int32_t no_tail;  /* 0: hybrid transparency (Eq. (15)); 1: inference without the tail
+                         (Sec. 4.4 ablation): C = sum_core alpha_i T_i c_i + T_{K+1} c_bg */
 } htgs_params;
 
 /* Tuning knobs (none changes the result beyond float rounding order) and
@@ -106,7 +108,8 @@ typedef struct {
  *           the blend adjoint and [2]/[3] around the preprocess adjoint. */
 typedef struct {
     int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 16x8 or 8x8 */
-    int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4 */
+    int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4
+                                 (1 when params.no_tail is set) */
     int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */
     int32_t smem_batch;       /* records the forward blend stages per shared-memory batch:
                                  32, 64 or 128 (default, also for 0) */

@@ -49,7 +49,7 @@ class Camera(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("tau_alpha", ctypes.c_float), ("tau_K", ctypes.c_float),
-                ("alpha_max", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+                ("alpha_max", ctypes.c_float), ("bg", ctypes.c_float * 3), ("no_tail", ctypes.c_int32)]
 
 
 class Launch(ctypes.Structure):
@@ -141,6 +141,7 @@ def c_params(p) -> Params:
     q.tau_alpha, q.tau_K, q.alpha_max = float(p.tau_alpha), float(p.tau_K), float(p.alpha_max)
     for i in range(3):
         q.bg[i] = float(p.bg[i])
+    q.no_tail = 1 if getattr(p, "no_tail", False) else 0
     return q
 
 

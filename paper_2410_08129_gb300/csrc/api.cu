@@ -145,6 +145,7 @@ void make_prm(const htgs_params *p, ParamArgs &a) {
     a.tau_K = p->tau_K;
     a.alpha_max = p->alpha_max;
     for (int i = 0; i < 3; ++i) a.bg[i] = p->bg[i];
+    a.no_tail = p->no_tail ? 1 : 0;
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }

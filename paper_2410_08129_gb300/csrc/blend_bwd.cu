@@ -7,14 +7,19 @@ namespace htgs {
 
 namespace {
 
-template <int TW, int TH>
+template <int TW, int TH, bool NOTAIL>
 bool run_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     const size_t smem = bwd_smem_bytes(TW * TH, a.prm.K);
-    if (!allow_dynamic_smem((const void *)blend_bwd_kernel<TW, TH>, bwd_smem_bytes(TW * TH, HTGS_MAX_K)))
-        return false;
-    const int grid = persistent_grid((const void *)blend_bwd_kernel<TW, TH>, kBwdThreads, smem, a.max_items);
-    blend_bwd_kernel<TW, TH><<<grid, kBwdThreads, smem, s>>>(b, a);
+    const void *fn = (const void *)blend_bwd_kernel<TW, TH, NOTAIL>;
+    if (!allow_dynamic_smem(fn, bwd_smem_bytes(TW * TH, HTGS_MAX_K))) return false;
+    const int grid = persistent_grid(fn, kBwdThreads, smem, a.max_items);
+    blend_bwd_kernel<TW, TH, NOTAIL><<<grid, kBwdThreads, smem, s>>>(b, a);
     return true;
+}
+
+template <int TW, int TH>
+bool run_bwd_mode(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
+    return a.prm.no_tail ? run_bwd<TW, TH, true>(b, a, s) : run_bwd<TW, TH, false>(b, a, s);
 }
 
 } // namespace
@@ -22,9 +27,9 @@ bool run_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
 bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     if (a.prm.K < 0 || a.prm.K > HTGS_MAX_K) return false;
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
-    if (tw == 16 && th == 16) return run_bwd<16, 16>(b, a, s);
-    if (tw == 16 && th == 8) return run_bwd<16, 8>(b, a, s);
-    if (tw == 8 && th == 8) return run_bwd<8, 8>(b, a, s);
+    if (tw == 16 && th == 16) return run_bwd_mode<16, 16>(b, a, s);
+    if (tw == 16 && th == 8) return run_bwd_mode<16, 8>(b, a, s);
+    if (tw == 8 && th == 8) return run_bwd_mode<8, 8>(b, a, s);
     return false;
 }
 

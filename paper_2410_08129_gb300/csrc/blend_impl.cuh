@@ -85,7 +85,7 @@ __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KM
 // ---------------------------------------------------------------------------
 // Forward (K6).
 // ---------------------------------------------------------------------------
-template <int KMAX, int TW, int TH, int PPT>
+template <int KMAX, int TW, int TH, int PPT, bool NOTAIL>
 __global__ void __launch_bounds__(TW *TH / PPT, (PPT == 1 && KMAX <= 8) ? 1024 / (TW * TH / PPT) : 1)
 blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
@@ -133,6 +133,7 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
 
     const int K = a.prm.K;
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
+    constexpr bool no_tail = NOTAIL;  // inference without the tail (compiled separately)
     float cz[PPT][KMAX];
     uint32_t cg[PPT][KMAX];
     float sA[PPT], sR[PPT], sG[PPT], sB[PPT], sP[PPT];
@@ -212,11 +213,13 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
                     FragEval f;
                     if (!frag_alpha(qd[p], tau_alpha, alpha_max, f)) continue;
                     const float al = f.alpha;
-                    sA[p] += al;
-                    sR[p] = __fmaf_rn(al, c5.x, sR[p]);
-                    sG[p] = __fmaf_rn(al, c5.y, sG[p]);
-                    sB[p] = __fmaf_rn(al, c5.z, sB[p]);
-                    sP[p] = __fmaf_rn(-sP[p], al, sP[p]);
+                    if (!no_tail) {  // without the tail the sums stay empty
+                        sA[p] += al;
+                        sR[p] = __fmaf_rn(al, c5.x, sR[p]);
+                        sG[p] = __fmaf_rn(al, c5.y, sG[p]);
+                        sB[p] = __fmaf_rn(al, c5.z, sB[p]);
+                        sP[p] = __fmaf_rn(-sP[p], al, sP[p]);
+                    }
                     nall[p] += 1;
                     if (al >= tau_K) {
                         ++n_adm;
@@ -413,7 +416,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
     return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float));
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool NOTAIL>
 __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
     constexpr int TP = TW * TH;
     constexpr int NW = kBwdThreads / 32;
@@ -624,6 +627,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                             in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
                         }
                     }
+                    if (NOTAIL && !in_core) continue;  // an omitted tail has no gradient
                     float dA, dc0, dc1, dc2;
                     if (in_core) {
                         const float4 PA = s_pa[p];
@@ -693,23 +697,23 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
 // ---------------------------------------------------------------------------
 // Dispatch over tile shape and pixels per thread for one KMAX.
 // ---------------------------------------------------------------------------
-template <int KMAX, int TW, int TH, int PPT>
+template <int KMAX, int TW, int TH, int PPT, bool NOTAIL>
 bool run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / PPT;
-    const void *fn = (const void *)blend_fwd_kernel<KMAX, TW, TH, PPT>;
+    const void *fn = (const void *)blend_fwd_kernel<KMAX, TW, TH, PPT, NOTAIL>;
     const size_t smem = fwd_smem_bytes(a.tiles.batch);
     if (!allow_dynamic_smem(fn, fwd_smem_bytes(128))) return false;
     const int grid = persistent_grid(fn, NT, smem, a.max_items);
-    blend_fwd_kernel<KMAX, TW, TH, PPT><<<grid, NT, smem, s>>>(b, a);
+    blend_fwd_kernel<KMAX, TW, TH, PPT, NOTAIL><<<grid, NT, smem, s>>>(b, a);
     return true;
 }
 
-template <int KMAX, int PPT>
+template <int KMAX, int PPT, bool NOTAIL = false>
 bool dispatch_shape_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
-    if (tw == 16 && th == 16) return run_fwd<KMAX, 16, 16, PPT>(b, a, s);
-    if (tw == 16 && th == 8 && PPT <= 2) return run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2)>(b, a, s);
-    if (tw == 8 && th == 8 && PPT <= 2) return run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2)>(b, a, s);
+    if (tw == 16 && th == 16) return run_fwd<KMAX, 16, 16, PPT, NOTAIL>(b, a, s);
+    if (tw == 16 && th == 8 && PPT <= 2) return run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2), NOTAIL>(b, a, s);
+    if (tw == 8 && th == 8 && PPT <= 2) return run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2), NOTAIL>(b, a, s);
     return false;
 }
 

@@ -25,6 +25,7 @@ struct ParamArgs {
     int K;
     float tau_alpha, tau_K, alpha_max;
     float bg[3];
+    int no_tail;  // 1: the tail is omitted (core over the background)
 };
 
 struct TileArgs {

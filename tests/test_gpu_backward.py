@@ -51,6 +51,18 @@ def test_small_scene_gradients(degree, K, tile, ppt):
     print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()}, "masked", (d["near_decision"] != 0).mean())
 
 
+def test_no_tail_gradients():
+    scene = scenes.small_box_scene(64, seed=7, sh_degree=1)
+    cam = scenes.identity_camera(1200, 800, 1200.0).crop(584, 384, 32, 32).rounded()
+    prm = scenes.Params(K=4, bg=(0.1, 0.2, 0.3), no_tail=True)
+    scene.means[:, :2] *= np.float32(0.04)
+    dl, d = _masked_upstream(scene, cam, prm, seed=11)
+    ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl.astype(np.float64))
+    got, _ = _gpu_grads(scene, cam, prm, dl)
+    rep = assert_grad_close(got, ref)
+    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()})
+
+
 def test_autograd_function_matches_direct_call():
     scene = scenes.small_box_scene(40, seed=9, sh_degree=1)
     cam = scenes.identity_camera(48, 40, 50.0).rounded()

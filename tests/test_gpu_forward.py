@@ -131,6 +131,25 @@ def test_k_values(K):
     assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS
 
 
+@pytest.mark.parametrize("K", [4, 16])
+def test_no_tail_matches_oracle(K):
+    """Inference without the tail: the core over the background."""
+    scene = scenes.small_box_scene(300, seed=5, sh_degree=1)
+    scene.log_scales += np.float32(0.4)
+    cam = scenes.identity_camera(80, 56, 70.0).rounded()
+    prm = scenes.Params(K=K, bg=(0.2, 0.3, 0.4), no_tail=True)
+    img, r, g = gpu_render(scene, cam, prm)
+    ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    e_ok, amb_frac, _ = compare_images(img, ref, d["ambiguous"])
+    assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS, (e_ok, amb_frac)
+    sv = saved_planes(r, cam, K)
+    ok = d["ambiguous"] == 0
+    np.testing.assert_array_equal(sv["core_gid"][ok], d["core_gid"][ok])
+    assert np.all(sv["A_tail"] == 0.0)
+    with_tail, *_ = gpu_render(scene, cam, scenes.Params(K=K, bg=(0.2, 0.3, 0.4)))
+    assert np.abs(with_tail - img).max() > 1e-3
+
+
 def test_core_ties_broken_by_gid():
     """Exact depth ties (duplicated Gaussians give bit-equal depths in FP32
     and FP64): the core is the K smallest (depth, gid) pairs. Gid order B, B,
