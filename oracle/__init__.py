@@ -112,7 +112,7 @@ def _load():
             lib.og_render_splats.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(_Camera), P(_Params),
                                              P(_Window), ctypes.c_void_p, P(_Diag)]
             lib.og_render_backward.argtypes = [P(_Gaussians), P(_Camera), P(_Params), P(_Window),
-                                               ctypes.c_void_p] + [ctypes.c_void_p] * 5
+                                               ctypes.c_void_p] + [ctypes.c_void_p] * 8
             lib.og_eval_pair.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_void_p]
             lib.og_sh_basis.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
@@ -249,9 +249,13 @@ def render(scene, cam, params, window=None, diagnostics: bool = False):
     return img
 
 
-def render_backward(scene, cam, params, dl_dimage, window=None):
+def render_backward(scene, cam, params, dl_dimage, window=None, stats: bool = False):
     """Analytic FP64 gradient of sum(dl_dimage * render(...)) over the window.
-    Returns a dict with means, log_scales, quats, opacity_logits and sh."""
+    Returns a dict with means, log_scales, quats, opacity_logits and sh; with
+    stats=True also the training statistics of the render: visibility (the
+    largest blending weight of each Gaussian over the window's pixels),
+    densify_grad (|dL/dmean| times half the distance to the camera, for
+    Gaussians covering pixels of the view) and densify_count (1 for those)."""
     lib = _load()
     keep = _Keep(scene)
     c, p = _camera(cam), _params(params)
@@ -260,10 +264,14 @@ def render_backward(scene, cam, params, dl_dimage, window=None):
     n = scene.means.shape[0]
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacity_logits=np.zeros(n), sh=np.zeros(scene.sh.shape))
+    if stats:
+        out.update(visibility=np.zeros(n), densify_grad=np.zeros(n), densify_count=np.zeros(n))
+    ptr = lambda k: out[k].ctypes.data if stats else None
     rc = lib.og_render_backward(ctypes.byref(keep.g), ctypes.byref(c), ctypes.byref(p),
                                 ctypes.byref(win), g.ctypes.data, out["means"].ctypes.data,
                                 out["log_scales"].ctypes.data, out["quats"].ctypes.data,
-                                out["opacity_logits"].ctypes.data, out["sh"].ctypes.data)
+                                out["opacity_logits"].ctypes.data, out["sh"].ctypes.data,
+                                ptr("visibility"), ptr("densify_grad"), ptr("densify_count"))
     if rc:
         raise RuntimeError(f"og_render_backward failed ({rc})")
     return out

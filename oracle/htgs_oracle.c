@@ -810,6 +810,7 @@ typedef struct {
     og_core_entry *core;  /* w*h*K */
     double *rec_grad;     /* n x 16: dr1[4], dr2[4], dr4[4], do, dc[3] */
     int err;
+    double *visibility;   /* n or NULL: largest blending weight over the window's pixels */
 } og_bwd_ctx;
 
 static void og_bwd_pixel_task(void *vctx, int64_t b, int64_t e) {
@@ -869,6 +870,7 @@ static void og_bwd_gauss_task(void *vctx, int64_t b, int64_t e) {
         const og_splat *sp = &c->sp[g];
         double *rg = c->rec_grad + g * 16;
         memset(rg, 0, 16 * sizeof(double));
+        if (c->visibility) c->visibility[g] = 0.0;
         if (!sp->valid) continue;
         for (int64_t pix = 0; pix < npix; ++pix) {
             int64_t li = pix % c->win.w, lj = pix / c->win.w;
@@ -891,6 +893,18 @@ static void og_bwd_gauss_task(void *vctx, int64_t b, int64_t e) {
                     for (int ch = 0; ch < 3; ++ch) dL_dc[ch] = st->g[ch] * ce->dc_coef;
                     break;
                 }
+            }
+            /* Blending weight of the fragment in the pixel colour: alpha_i T_i in
+               the core, T_core (1 - T_tail) alpha_j / A in the tail. */
+            if (c->visibility) {
+                double w = 0.0;
+                if (in_core) {
+                    for (int k = 0; k < st->n_core && k < K; ++k)
+                        if (c->core[pix * K + k].gid == g) w = c->core[pix * K + k].dc_coef;
+                } else if (!c->prm->no_tail && st->A_tail > 0) {
+                    w = st->T_core * (1.0 - st->T_tail) * alpha / st->A_tail;
+                }
+                if (w > c->visibility[g]) c->visibility[g] = w;
             }
             if (!in_core && c->prm->no_tail) continue; /* an omitted tail has no gradient */
             if (!in_core) {
@@ -947,6 +961,7 @@ typedef struct {
     const og_camera *cam;
     const double *rec_grad;
     double *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
+    double *densify_grad, *densify_count; /* n or NULL */
 } og_chain_ctx;
 
 /* Chain rule from (dT'_1, dT'_2, dT'_4, do, dc) to the parameters. */
@@ -1031,6 +1046,14 @@ static void og_chain_task(void *vctx, int64_t b, int64_t e) {
             double pd = ddir[0] * sp->dir[0] + ddir[1] * sp->dir[1] + ddir[2] * sp->dir[2];
             for (int j = 0; j < 3; ++j) dmu[j] += (ddir[j] - sp->dir[j] * pd) / sp->dist;
         }
+        /* Densification statistic (Sec. 4.2, after Moenne-Loccoz et al.): the
+           norm of the mean's gradient times half the distance to the camera,
+           for a Gaussian that covers pixels of this view. */
+        if (sp->rect[0] <= sp->rect[1] && sp->rect[2] <= sp->rect[3]) {
+            if (c->densify_grad)
+                c->densify_grad[i] = 0.5 * sp->dist * sqrt(dmu[0] * dmu[0] + dmu[1] * dmu[1] + dmu[2] * dmu[2]);
+            if (c->densify_count) c->densify_count[i] = 1.0;
+        }
     }
 }
 
@@ -1039,7 +1062,8 @@ static void og_chain_task(void *vctx, int64_t b, int64_t e) {
 int og_render_backward(const og_gaussians *g, const og_camera *cam, const og_params *prm,
                        const og_window *win, const double *dl_dimg,
                        double *d_means, double *d_log_scales, double *d_quats,
-                       double *d_logits, double *d_sh) {
+                       double *d_logits, double *d_sh,
+                       double *visibility, double *densify_grad, double *densify_count) {
     if (!g || og_check(cam, prm, win) || !dl_dimg) return 1;
     if (!d_means || !d_log_scales || !d_quats || !d_logits || !d_sh) return 1;
     if (prm->K > 64) return 1;
@@ -1054,13 +1078,16 @@ int og_render_backward(const og_gaussians *g, const og_camera *cam, const og_par
     if (!sp || !pix || !core || !rec) rc = 2;
     if (!rc) rc = og_preprocess(g, cam, prm, sp);
     if (!rc) {
-        og_bwd_ctx c = {sp, n, cam, prm, *win, dl_dimg, pix, core, rec, 0};
+        og_bwd_ctx c = {sp, n, cam, prm, *win, dl_dimg, pix, core, rec, 0, visibility};
         og_parallel_for(npix, 4, og_bwd_pixel_task, &c);
         if (c.err) rc = 2;
         if (!rc) og_parallel_for(n, 8, og_bwd_gauss_task, &c);
     }
     if (!rc) {
-        og_chain_ctx cc = {g, sp, cam, rec, d_means, d_log_scales, d_quats, d_logits, d_sh};
+        if (densify_grad) memset(densify_grad, 0, (size_t)n * sizeof(double));
+        if (densify_count) memset(densify_count, 0, (size_t)n * sizeof(double));
+        og_chain_ctx cc = {g, sp, cam, rec, d_means, d_log_scales, d_quats, d_logits, d_sh,
+                           densify_grad, densify_count};
         og_parallel_for(n, 1024, og_chain_task, &cc);
     }
     free(sp);

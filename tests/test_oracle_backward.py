@@ -100,3 +100,58 @@ def test_window_gradients_add_up():
     b = oracle.render_backward(scene, cam, prm, g[:, 10:], window=(10, 0, 14, 16))
     for k in full:
         np.testing.assert_allclose(full[k], a[k] + b[k], rtol=1e-10, atol=1e-12)
+
+
+def _weights_sorted(frags):
+    """Blending weights alpha_i T_i of a depth-sorted fragment list (Eq. (2))."""
+    out, T = {}, 1.0
+    for z, gid, a, c in sorted(frags, key=lambda f: (f[0], f[1])):
+        out[gid] = max(out.get(gid, 0.0), a * T)
+        T *= 1.0 - a
+    return out
+
+
+@pytest.mark.parametrize("K,tau_K", [(64, 0.0), (0, 0.05)])
+def test_visibility_is_the_largest_blending_weight(K, tau_K):
+    """With K >= |F| and tau_K = 0 the weights are those of sorted alpha
+    blending; with K = 0 every fragment is in the tail and weighs
+    (1 - prod(1 - a)) a_j / sum(a)."""
+    from tests.test_oracle_blend import _independent_fragments
+    scene = scenes.small_box_scene(12, seed=500 + K, sh_degree=0).astype(np.float64)
+    scene.log_scales += 0.6
+    cam = scenes.identity_camera(20, 16, 20.0)
+    prm = scenes.Params(K=K, tau_K=tau_K)
+    out = oracle.render_backward(scene, cam, prm, np.ones((16, 20, 3)), stats=True)
+    want = np.zeros(scene.n)
+    for j in range(cam.height):
+        for i in range(cam.width):
+            fr = _independent_fragments(scene, cam, prm, i + 0.5, j + 0.5)
+            if K:
+                w = _weights_sorted(fr)
+            else:
+                A = sum(f[2] for f in fr)
+                Tt = float(np.prod([1.0 - f[2] for f in fr]))
+                w = {f[1]: (1.0 - Tt) * f[2] / A for f in fr} if A > 0 else {}
+            for gid, v in w.items():
+                want[gid] = max(want[gid], v)
+    assert want.max() > 0.1
+    np.testing.assert_allclose(out["visibility"], want, rtol=1e-10, atol=1e-14)
+
+
+def test_densification_statistic_is_half_distance_times_mean_gradient():
+    scene = scenes.small_box_scene(30, seed=510, sh_degree=1).astype(np.float64)
+    scene.log_scales += 0.4
+    scene.means[:4, 0] += 20.0  # outside the view
+    cam = scenes.fov_camera(scenes.look_at((0.3, -0.2, -0.5), (0.0, 0.0, 3.0)), 32, 24, 60.0)
+    prm = scenes.Params(K=3)
+    g = np.random.default_rng(3).standard_normal((24, 32, 3))
+    out = oracle.render_backward(scene, cam, prm, g, stats=True)
+    M = np.asarray(cam.world_to_cam)
+    centre = -M[:3, :3].T @ M[:3, 3]
+    dist = np.linalg.norm(scene.means - centre, axis=1)
+    sp = oracle.preprocess(scene, cam, prm)
+    covers = (sp["valid"] == 1) & (sp["rect"][:, 0] <= sp["rect"][:, 1]) & (sp["rect"][:, 2] <= sp["rect"][:, 3])
+    assert 0 < covers.sum() < scene.n
+    np.testing.assert_array_equal(out["densify_count"], covers.astype(float))
+    want = np.where(covers, 0.5 * dist * np.linalg.norm(out["means"], axis=1), 0.0)
+    np.testing.assert_allclose(out["densify_grad"], want, rtol=1e-12, atol=0)
