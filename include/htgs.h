@@ -68,13 +68,26 @@ typedef struct {
     const float *filter_var;
 } htgs_gaussians;
 
-/* Gradient outputs, same shapes as htgs_gaussians. Device pointers. */
+/* Gradient outputs, same shapes as htgs_gaussians. Device pointers.
+ * The last three are optional training statistics of the render (NULL to
+ * skip; n floats each, caller-initialised, accumulated across calls):
+ *   visibility     max(visibility, largest blending weight of the Gaussian in
+ *                  any pixel): alpha_i T_i in the core, T_core (1 - T_tail)
+ *                  alpha_j / A in the tail (the visibility score of Sec. 4.2,
+ *                  after Niemeyer et al.); non-negative
+ *   densify_grad   += |dL/dmean| times half the distance from the camera, per
+ *                  view whose pixels the Gaussian covers (Sec. 4.2, after
+ *                  Moenne-Loccoz et al.)
+ *   densify_count  += 1 per such view */
 typedef struct {
     float *means;
     float *log_scales;
     float *quats;
     float *opacity_logits;
     float *sh;
+    float *visibility;
+    float *densify_grad;
+    float *densify_count;
 } htgs_gaussians_grad;
 
 /* Pinhole camera, OpenCV axes (+x right, +y down, +z forward); world_to_cam

@@ -38,7 +38,8 @@ class Gaussians(ctypes.Structure):
 class GaussiansGrad(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
-                ("sh", ctypes.c_void_p)]
+                ("sh", ctypes.c_void_p), ("visibility", ctypes.c_void_p),
+                ("densify_grad", ctypes.c_void_p), ("densify_count", ctypes.c_void_p)]
 
 
 class Camera(ctypes.Structure):

@@ -27,7 +27,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     // byte offsets inside the workspace
     size_t status, stats, total, work, ghist, tickets, ranges, lookback, n_items, done, zero_end;
-    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, end;
+    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, vis, end;
     int n_blocks, n_sort_blocks, passes, digit_bits, slots_cap, max_items;
     TileArgs tiles;
     int64_t n_rec;
@@ -123,6 +123,7 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     o = align_up(o + (size_t)L.slots_cap * (6 + 2 * prm->K) * L.tiles.tile_w * L.tiles.tile_h * sizeof(float));
     L.bwd_work = o; o = align_up(o + 4 * sizeof(uint32_t));
     L.acc = o; o = align_up(o + (size_t)n_rec * 16 * sizeof(float));
+    L.vis = o; o = align_up(o + (size_t)n_rec * sizeof(float));
     L.end = o;
     return HTGS_OK;
 }
@@ -208,6 +209,12 @@ void make_batch(int n_views, const htgs_view *views, const Layout &L, bool backw
             d.dl_dimg = hv.dl_dimage;
             d.g_means = hv.grads->means; d.g_log_scales = hv.grads->log_scales;
             d.g_quats = hv.grads->quats; d.g_logits = hv.grads->opacity_logits; d.g_sh = hv.grads->sh;
+            d.g_vis = hv.grads->visibility; d.g_dgrad = hv.grads->densify_grad;
+            d.g_dcount = hv.grads->densify_count;
+        } else {
+            d.dl_dimg = nullptr;
+            d.g_means = d.g_log_scales = d.g_quats = d.g_logits = d.g_sh = nullptr;
+            d.g_vis = d.g_dgrad = d.g_dcount = nullptr;
         }
         rec += g->n;
         tile += d.tiles_x * d.tiles_y;
@@ -368,6 +375,9 @@ htgs_status render_batch_backward(int n_views, const htgs_view *views, const htg
     bb.work = at<unsigned int>(workspace, L.bwd_work);
     bb.tiles = L.tiles; bb.prm = pa;
     bb.acc = acc;
+    bool want_vis = false;
+    for (int v = 0; v < n_views; ++v) want_vis = want_vis || views[v].grads->visibility;
+    bb.vis = want_vis ? at<float>(workspace, L.vis) : nullptr;
     mark(launch, 0, s);
     if (!launch_blend_bwd(b, bb, s)) return HTGS_ERR_NOT_SUPPORTED;
     mark(launch, 1, s);
@@ -378,6 +388,7 @@ htgs_status render_batch_backward(int n_views, const htgs_view *views, const htg
         pb.rec = at<float4>(workspace, L.rec);
         pb.rect = at<uint2>(workspace, L.rect);
         pb.acc = acc;
+        pb.vis = bb.vis;
         pb.accumulate = accumulate ? 1 : 0;
         preprocess_backward_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(b, pb);
     }

@@ -413,10 +413,10 @@ __device__ __forceinline__ void warp_reduce16_to4(float (&v)[16], int lane) {
 
 // Dynamic shared memory of the adjoint for a TP-pixel tile and core size K.
 __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
-    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float));
+    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float) + sizeof(float));
 }
 
-template <int TW, int TH, bool NOTAIL>
+template <int TW, int TH, bool NOTAIL, bool VIS>
 __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
     constexpr int TP = TW * TH;
     constexpr int NW = kBwdThreads / 32;
@@ -435,6 +435,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     uint32_t *s_cg = reinterpret_cast<uint32_t *>(s_pc + TP);        // [K][TP] core gids
     float *s_cw = reinterpret_cast<float *>(s_cg + (size_t)K * TP);  // [K][TP] dL/dalpha_r
     float *s_cv = s_cw + (size_t)K * TP;                             // [K][TP] alpha_r T_r
+    float *s_wt = s_cv + (size_t)K * TP;                             // [TP] T_core (1 - T_tail) / A
     if (a.status[kStError] != 0) return;
 
     // Persistent CTA: take (view, tile, chunk) items from the shared queue.
@@ -489,6 +490,8 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             ct2 = saved[6 * npix + pix];
         }
         float u0 = 0.f, u1 = 0.f, u2 = 0.f, k0 = 0.f, k1 = 0.f;
+        // A tail fragment's blending weight is alpha_j T_core (1 - T_tail) / A.
+        s_wt[p] = At > 0.f ? __fdividef(Tc - Pc, At) : 0.f;
         if (At > 0.f) {
             const float s = __fdividef(Tc - Pc, At);
             u0 = g0 * s; u1 = g1 * s; u2 = g2 * s;
@@ -600,6 +603,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
             float gaa = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+            float wmax = 0.f;  // largest blending weight of the record in this tile
             bool touched = false;
             const int lx = lane & 7, ly = lane >> 3;
             for (int by = iy0; by <= iy1; by += 4) {
@@ -640,12 +644,14 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                             }
                         dA = w;
                         dc0 = PA.x * s; dc1 = PA.y * s; dc2 = PA.z * s;
+                        if (VIS) wmax = fmaxf(wmax, s);
                     } else {
                         const float4 PB = s_pb[p];
                         const float k0 = s_pa[p].w;
                         const float inv = rcp_approx(1.f - al);
                         dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + k0 + PB.w * inv;
                         dc0 = PB.x * al; dc1 = PB.y * al; dc2 = PB.z * al;
+                        if (VIS) wmax = fmaxf(wmax, al * s_wt[p]);
                     }
                     touched = true;
                     gc0 += dc0; gc1 += dc1; gc2 += dc2;
@@ -670,6 +676,11 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                         acc[5] = ffma2(ey, Y, acc[5]);
                     }
                 }
+            }
+            if (VIS) {
+                for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+                // Non-negative floats order like their bit patterns.
+                if (lane == 0 && wmax > 0.f) atomicMax(reinterpret_cast<int *>(a.vis) + gid, __float_as_int(wmax));
             }
             if (__any_sync(0xffffffffu, touched)) {
                 float v[16] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y,

@@ -37,6 +37,7 @@ struct ViewDesc {
     const float *means, *log_scales, *quats, *logits, *sh;
     const float *filter_var;  // nullptr: no 3D filter
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+    float *g_vis, *g_dgrad, *g_dcount;  // optional training statistics
     float *image;          // H x W x 3
     float *saved;          // (7 + K) planes of H*W, or nullptr
     const float *dl_dimg;  // H x W x 3 (backward)
@@ -90,6 +91,7 @@ struct PreBwdArgs {
     const float4 *rec;
     const uint2 *rect;
     const float *acc;      // n_rec * 16
+    const float *vis;      // n_rec: largest blending weight of each record, or nullptr
     int accumulate;        // 1: several views share a scene, add into the gradients atomically
 };
 
@@ -178,6 +180,7 @@ struct BlendBwdArgs {
     TileArgs tiles;
     ParamArgs prm;
     float *acc;            // n_rec * 16
+    float *vis;            // n_rec (largest blending weight, as int bits), or nullptr
 };
 
 __global__ void preprocess_kernel(const __grid_constant__ Batch b, PreArgs a);

@@ -532,6 +532,15 @@ preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
         const float id = 1.f / S.dist;
         for (int k = 0; k < 3; ++k) gmu[k] += (gd[k] - S.dir[k] * pd) * id;
     }
+    // Training statistics of this view (Sec. 4.2): the mean's gradient times
+    // half the camera distance, the view count and the largest blending weight.
+    if (V.g_dgrad)
+        atomicAdd(V.g_dgrad + g, 0.5f * S.dist * sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]));
+    if (V.g_dcount) atomicAdd(V.g_dcount + g, 1.f);
+    if (V.g_vis && a.vis) {
+        const float w = a.vis[i];
+        if (w > 0.f) atomicMax(reinterpret_cast<int *>(V.g_vis) + g, __float_as_int(w));
+    }
     emit();
 }
 

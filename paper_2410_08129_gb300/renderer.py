@@ -12,6 +12,21 @@ import torch
 from . import binding as B
 
 FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+# Optional training statistics written by the backward (one float per Gaussian).
+STATS = ("visibility", "densify_grad", "densify_count")
+
+
+def _c_grad(grads, stats=None) -> B.GaussiansGrad:
+    """htgs_gaussians_grad of gradient tensors and optional statistic tensors
+    (see htgs_gaussians_grad: visibility is max-combined, the densification
+    sums are added to, so the caller initialises them)."""
+    ptrs = [B._ptr(grads[f]).value for f in FIELDS]
+    for k in STATS:
+        t = (stats or {}).get(k)
+        if t is not None and (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"{k} must be a contiguous float32 CUDA tensor")
+        ptrs.append(B._ptr(t).value if t is not None else None)
+    return B.GaussiansGrad(*ptrs)
 
 
 def _grown_capacity(needed: int, current: int) -> int:
@@ -105,13 +120,14 @@ class Renderer:
             return image
         raise B.HTGSError(B.HTGS_ERR_OVERFLOW, "htgs_render")
 
-    def backward(self, g: GaussianTensors, dl_dimage: torch.Tensor, grads=None, stream=None):
+    def backward(self, g: GaussianTensors, dl_dimage: torch.Tensor, grads=None, stream=None, stats=None):
+        """stats: optional dict of float32 (N,) tensors keyed by STATS."""
         dl = dl_dimage.contiguous()
         if dl.dtype != torch.float32 or tuple(dl.shape) != (self.camera.height, self.camera.width, 3):
             raise ValueError("dl_dimage must be float32 of shape (H, W, 3)")
         if grads is None:
             grads = {f: torch.empty_like(getattr(g, f)) for f in FIELDS}
-        cgrad = B.GaussiansGrad(*[B._ptr(grads[f]).value for f in FIELDS])
+        cgrad = _c_grad(grads, stats)
         st = B.htgs_render_backward(g.c_struct(), self.camera, self.params, self.launch, self.workspace,
                                     self.capacity, self.saved, dl, cgrad, stream)
         B._check(st, "htgs_render_backward")
@@ -175,11 +191,11 @@ class BatchRenderer:
             self._structs[key] = g.c_struct()
         return self._structs[key]
 
-    def views(self, dl_dimages=None, grads=None):
+    def views(self, dl_dimages=None, grads=None, stats=None):
         gs = [self._struct(s) for s in self.scenes]
         cg = None
         if grads is not None:
-            cg = [B.GaussiansGrad(*[B._ptr(grads[id(s)][f]).value for f in FIELDS]) for s in self.scenes]
+            cg = [_c_grad(grads[id(s)], (stats or {}).get(id(s))) for s in self.scenes]
         return B.c_views(gs, self.cameras, self.images, self.saved, dl_dimages, cg)
 
     def _alloc(self):
@@ -211,11 +227,12 @@ class BatchRenderer:
                 out[id(s)] = {f: torch.empty_like(getattr(s, f)) for f in FIELDS}
         return out
 
-    def backward(self, dl_dimages, grads=None, stream=None):
+    def backward(self, dl_dimages, grads=None, stream=None, stats=None):
+        """stats: optional {id(scene): {statistic: float32 (N,) tensor}}."""
         if grads is None:
             grads = self.gradient_buffers()
         dls = [d.contiguous() for d in dl_dimages]
-        views = self.views(dl_dimages=dls, grads=grads)
+        views = self.views(dl_dimages=dls, grads=grads, stats=stats)
         B._check(B.htgs_render_batch_backward(views, self.params, self.launch, self.workspace, self.capacity,
                                               stream), "htgs_render_batch_backward")
         return grads

@@ -1,0 +1,78 @@
+"""Training statistics written by the render backward (Sec. 4.2): the
+largest blending weight of every Gaussian (visibility score), the norm of the
+mean's gradient times half the camera distance, and the number of views a
+Gaussian covers. Against the FP64 oracle on one view, and combined over the
+views of a batch exactly as over separate calls (max, sum, count)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_08129_gb300 import scenes
+from paper_2410_08129_gb300.renderer import STATS, BatchRenderer, GaussianTensors, Renderer
+
+pytestmark = pytest.mark.gpu
+
+
+def _zeros(n):
+    return {k: torch.zeros(n, dtype=torch.float32, device="cuda") for k in STATS}
+
+
+@pytest.mark.parametrize("K", [4, 0])
+def test_statistics_match_oracle(K):
+    scene = scenes.small_box_scene(120, seed=60 + K, sh_degree=1)
+    scene.log_scales += np.float32(0.3)
+    scene.means[:10, 0] += np.float32(20.0)  # outside the view
+    cam = scenes.fov_camera(scenes.look_at((0.2, -0.1, -0.4), (0.0, 0.0, 3.0)), 64, 48, 60.0).rounded()
+    prm = scenes.Params(K=K, bg=(0.1, 0.2, 0.3))
+    _, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    dl = np.random.default_rng(K).standard_normal((cam.height, cam.width, 3))
+    dl[d["near_decision"] != 0] = 0.0
+    ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl, stats=True)
+    g = GaussianTensors.from_scene(scene)
+    r = Renderer(cam, prm, scene.n)
+    r.forward(g)
+    st = _zeros(scene.n)
+    grads = r.backward(g, torch.as_tensor(dl, dtype=torch.float32).cuda(), stats=st)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in st.items()}
+    np.testing.assert_array_equal(got["densify_count"], ref["densify_count"])
+    assert 0 < ref["densify_count"].sum() < scene.n
+    # visibility: FP32 weights; a near-decision at a Gaussian's heaviest pixel may move it further
+    vis_err = np.abs(got["visibility"] - ref["visibility"]) > 2e-4 + 2e-3 * ref["visibility"]
+    assert vis_err.mean() <= 0.03, (vis_err.sum(), np.abs(got["visibility"] - ref["visibility"]).max())
+    assert ref["visibility"].max() > 0.1
+    # the densification statistic follows the mean gradient (1e-3 relative per tensor)
+    gm = grads["means"].cpu().numpy().astype(np.float64)
+    scale = np.abs(ref["densify_grad"]).max()
+    assert np.linalg.norm(got["densify_grad"] - ref["densify_grad"]) <= 1e-3 * np.linalg.norm(ref["densify_grad"])
+    M = np.asarray(cam.world_to_cam)
+    centre = -M[:3, :3].T @ M[:3, 3]
+    dist = np.linalg.norm(scene.means.astype(np.float64) - centre, axis=1)
+    own = np.where(got["densify_count"] > 0, 0.5 * dist * np.linalg.norm(gm, axis=1), 0.0)
+    np.testing.assert_allclose(got["densify_grad"], own, rtol=1e-4, atol=1e-6 * scale)
+
+
+def test_statistics_combine_over_batch_views():
+    scene = scenes.small_box_scene(3000, seed=64, sh_degree=1)
+    g = GaussianTensors.from_scene(scene)
+    cams = [scenes.fov_camera(scenes.look_at((0.6 * i - 0.6, 0.1, -0.8), (0.0, 0.0, 3.0)), 96, 72, 60.0)
+            .rounded() for i in range(3)]
+    prm = scenes.Params(K=8)
+    br = BatchRenderer([g] * 3, cams, prm)
+    br.forward()
+    dls = [torch.randn(im.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(i))
+           for i, im in enumerate(br.images)]
+    st = _zeros(scene.n)
+    br.backward(dls, stats={id(g): st})
+    want = _zeros(scene.n)
+    for cam, dl in zip(cams, dls):
+        r = Renderer(cam, prm, scene.n)
+        r.forward(g)
+        r.backward(g, dl, stats=want)
+    torch.cuda.synchronize()
+    assert torch.equal(st["densify_count"], want["densify_count"])
+    assert int(want["densify_count"].max()) == 3
+    torch.testing.assert_close(st["visibility"], want["visibility"], rtol=1e-5, atol=1e-7)
+    torch.testing.assert_close(st["densify_grad"], want["densify_grad"], rtol=1e-4,
+                               atol=1e-6 * float(want["densify_grad"].abs().max()))
