@@ -39,6 +39,7 @@ _lib = None
 _lock = threading.Lock()
 
 AMB_CUTOFF, AMB_TAUK, AMB_AMAX, AMB_CORE_EDGE, AMB_CORE_TIE, AMB_DEN = 1, 2, 4, 8, 16, 32
+AMB_TERM, AMB_ORDER = 64, 128
 
 
 def build(force: bool = False) -> str:
@@ -70,7 +71,8 @@ class _Camera(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("tau_alpha", ctypes.c_double), ("tau_K", ctypes.c_double),
-                ("alpha_max", ctypes.c_double), ("bg", ctypes.c_double * 3), ("no_tail", ctypes.c_int32)]
+                ("alpha_max", ctypes.c_double), ("bg", ctypes.c_double * 3), ("no_tail", ctypes.c_int32),
+                ("sorted_blend", ctypes.c_int32)]
 
 
 class _Window(ctypes.Structure):
@@ -175,6 +177,7 @@ def _params(p) -> _Params:
     for i in range(3):
         q.bg[i] = float(p.bg[i])
     q.no_tail = 1 if getattr(p, "no_tail", False) else 0
+    q.sorted_blend = 1 if getattr(p, "sorted_blend", False) else 0
     return q
 
 

@@ -63,6 +63,8 @@ typedef struct {
     double tau_alpha, tau_K, alpha_max;
     double bg[3];
     int32_t no_tail; /* 1: inference without the tail (Sec. 4.4): C = core + T_{K+1} bg */
+    int32_t sorted_blend; /* 1: Tab. 3 "w/o per-pixel HT": fragments in order of their Gaussian's
+                             view-space mean depth, sorted alpha blending, early termination */
 } og_params;
 
 typedef struct {
@@ -118,8 +120,12 @@ enum {
     OG_AMB_AMAX = 4,     /* |o e^{-rho^2/2} - alpha_max| <= 1e-6 */
     OG_AMB_CORE_EDGE = 8,/* K-th and (K+1)-th candidate depths within 1e-5 |z| */
     OG_AMB_CORE_TIE = 16,/* two adjacent core depths within 1e-5 |z| */
-    OG_AMB_DEN = 32      /* ray nearly parallel to a flat splat: den tiny relative to its scale */
+    OG_AMB_DEN = 32,     /* ray nearly parallel to a flat splat: den tiny relative to its scale */
+    OG_AMB_TERM = 64,    /* sorted blending: T (1 - alpha) within 1e-6 relative of the termination threshold */
+    OG_AMB_ORDER = 128   /* sorted blending: two used fragments' mean depths within 1e-5 |z| */
 };
+/* Sorted blending stops before the fragment that would take T below this. */
+#define OG_SORTED_TMIN 1e-4
 #define OG_CUTOFF_REL 2e-5
 #define OG_TAUK_ABS 2e-6
 #define OG_AMAX_ABS 1e-6
@@ -482,6 +488,7 @@ typedef struct {
     double c[3];
     int64_t gid;
     int32_t force; /* 0: core admission by alpha >= tau_K; +1 / -1: forced in / out */
+    double zmean;  /* view-space depth of the Gaussian's mean (sorted blending) */
 } og_frag;
 
 static int og_frag_cmp(const void *pa, const void *pb) {
@@ -523,6 +530,7 @@ static int og_fragment(const og_splat *sp, int64_t gid, double xs, double ys, co
     const int kept = ev.rho2 <= rc;
     if (!kept && !near_cut) return 0;
     fr->z = ev.z;
+    fr->zmean = sp->MT[2][3];
     fr->rho2 = ev.rho2;
     fr->a_raw = sp->o * exp(-0.5 * ev.rho2);
     fr->alpha = fr->a_raw < prm->alpha_max ? fr->a_raw : prm->alpha_max;
@@ -558,9 +566,52 @@ static uint64_t og_mix(uint64_t x) {
     return x;
 }
 
+static int og_frag_cmp_mean(const void *pa, const void *pb) {
+    const og_frag *a = (const og_frag *)pa, *b = (const og_frag *)pb;
+    if (a->zmean < b->zmean) return -1;
+    if (a->zmean > b->zmean) return 1;
+    return (a->gid > b->gid) - (a->gid < b->gid);
+}
+
+/* Tab. 3 "w/o per-pixel HT": the perspective-correct fragments blended front
+   to back in the order of their Gaussians' view-space mean depth (then gid),
+   Eq. (2) plus background, stopping before the fragment that would take the
+   transmittance below OG_SORTED_TMIN. On return F->f[0 .. n_core) holds the
+   blended fragments in order (the "core"; there is no tail). */
+static void og_blend_sorted(og_fragvec *F, const og_params *prm, og_pixel_result *res) {
+    res->n_frag = F->n;
+    res->hash = 0;
+    for (int64_t i = 0; i < F->n; ++i) res->hash += og_mix((uint64_t)F->f[i].gid + 0x9e3779b97f4a7c15ULL);
+    qsort(F->f, (size_t)F->n, sizeof(og_frag), og_frag_cmp_mean);
+    double C[3] = {0, 0, 0}, T = 1.0;
+    int64_t used = 0;
+    for (int64_t i = 0; i < F->n; ++i) {
+        const og_frag *f = &F->f[i];
+        const double Tn = T * (1.0 - f->alpha);
+        if (fabs(Tn - OG_SORTED_TMIN) <= 1e-6 * OG_SORTED_TMIN + 1e-7 * T) res->amb |= OG_AMB_TERM;
+        if (Tn < OG_SORTED_TMIN) break;
+        if (i > 0 && fabs(f->zmean - F->f[i - 1].zmean) <= OG_DEPTH_REL * fabs(f->zmean)) res->amb |= OG_AMB_ORDER;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += f->alpha * T * f->c[ch];
+        T = Tn;
+        ++used;
+    }
+    res->n_core = used;
+    res->T_core = T;
+    res->T_tail = 1.0;
+    res->A_tail = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+        res->c_tail[ch] = 0.0;
+        res->C[ch] = C[ch] + T * prm->bg[ch];
+    }
+}
+
 /* Splits the fragment list F into core and tail and composites, Eq. (15)-(16).
    On return F->f[0 .. n_core) holds the core in depth order. */
 static void og_blend(og_fragvec *F, const og_params *prm, og_pixel_result *res) {
+    if (prm->sorted_blend) {
+        og_blend_sorted(F, prm, res);
+        return;
+    }
     const int K = prm->K;
     res->n_frag = F->n;
     res->hash = 0;
@@ -718,7 +769,7 @@ static void og_render_task(void *vctx, int64_t b, int64_t e) {
             int64_t nc = 0;
             while (nc < F.n && (F.f[nc].force > 0 || (F.f[nc].force == 0 && F.f[nc].alpha >= c->prm->tau_K))) ++nc;
             Fs.n = nc < K + 1 ? nc : K + 1;
-            int32_t amb = near & (OG_AMB_DEN);
+            int32_t amb = near & (OG_AMB_DEN | OG_AMB_TERM | OG_AMB_ORDER);
             if (near & (OG_AMB_CUTOFF | OG_AMB_TAUK | OG_AMB_CORE_EDGE | OG_AMB_CORE_TIE))
                 amb |= og_effects(&F0, &Bd, &Fs, &res, c->prm, &work, &scratch);
             if (d->n_frag) d->n_frag[pix] = (int32_t)res.n_frag;
@@ -811,12 +862,15 @@ typedef struct {
     double *rec_grad;     /* n x 16: dr1[4], dr2[4], dr4[4], do, dc[3] */
     int err;
     double *visibility;   /* n or NULL: largest blending weight over the window's pixels */
+    int64_t kcap;         /* per-pixel entries of core: K, or n for sorted blending */
 } og_bwd_ctx;
 
 static void og_bwd_pixel_task(void *vctx, int64_t b, int64_t e) {
     og_bwd_ctx *c = (og_bwd_ctx *)vctx;
     og_fragvec F = {0};
-    const int K = c->prm->K;
+    const int64_t K = c->kcap;
+    double *Ti = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+    if (!Ti) { c->err = 1; return; }
     for (int64_t pix = b; pix < e; ++pix) {
         int64_t li = pix % c->win.w, lj = pix / c->win.w;
         double xs = (double)(c->win.x0 + li) + 0.5;
@@ -844,7 +898,6 @@ static void og_bwd_pixel_task(void *vctx, int64_t b, int64_t e) {
         double G[3];
         for (int ch = 0; ch < 3; ++ch)
             G[ch] = (1.0 - res.T_tail) * res.c_tail[ch] + res.T_tail * c->prm->bg[ch];
-        double Ti[64];
         double T = 1.0;
         for (int64_t i = 0; i < res.n_core; ++i) { Ti[i] = T; T *= 1.0 - F.f[i].alpha; }
         for (int64_t i = res.n_core - 1; i >= 0; --i) {
@@ -860,11 +913,12 @@ static void og_bwd_pixel_task(void *vctx, int64_t b, int64_t e) {
         for (int64_t i = res.n_core; i < K; ++i) c->core[pix * K + i].gid = -1;
     }
     free(F.f);
+    free(Ti);
 }
 
 static void og_bwd_gauss_task(void *vctx, int64_t b, int64_t e) {
     og_bwd_ctx *c = (og_bwd_ctx *)vctx;
-    const int K = c->prm->K;
+    const int64_t K = c->kcap;
     const int64_t npix = (int64_t)c->win.w * c->win.h;
     for (int64_t g = b; g < e; ++g) {
         const og_splat *sp = &c->sp[g];
@@ -901,12 +955,13 @@ static void og_bwd_gauss_task(void *vctx, int64_t b, int64_t e) {
                 if (in_core) {
                     for (int k = 0; k < st->n_core && k < K; ++k)
                         if (c->core[pix * K + k].gid == g) w = c->core[pix * K + k].dc_coef;
-                } else if (!c->prm->no_tail && st->A_tail > 0) {
+                } else if (!c->prm->no_tail && !c->prm->sorted_blend && st->A_tail > 0) {
                     w = st->T_core * (1.0 - st->T_tail) * alpha / st->A_tail;
                 }
                 if (w > c->visibility[g]) c->visibility[g] = w;
             }
-            if (!in_core && c->prm->no_tail) continue; /* an omitted tail has no gradient */
+            /* An omitted tail, or fragments behind the early termination, have no gradient. */
+            if (!in_core && (c->prm->no_tail || c->prm->sorted_blend)) continue;
             if (!in_core) {
                 const double Tc = st->T_core, Tt = st->T_tail, A = st->A_tail;
                 for (int ch = 0; ch < 3; ++ch) {
@@ -1066,19 +1121,21 @@ int og_render_backward(const og_gaussians *g, const og_camera *cam, const og_par
                        double *visibility, double *densify_grad, double *densify_count) {
     if (!g || og_check(cam, prm, win) || !dl_dimg) return 1;
     if (!d_means || !d_log_scales || !d_quats || !d_logits || !d_sh) return 1;
-    if (prm->K > 64) return 1;
+    if (!prm->sorted_blend && prm->K > 64) return 1;
+    const int64_t kcap = prm->sorted_blend ? (g->n > 0 ? g->n : 1) : (prm->K > 0 ? prm->K : 1);
+    if ((double)win->w * win->h * kcap > 2e8) return 1;
     const int64_t n = g->n;
     const int64_t npix = (int64_t)win->w * win->h;
     og_splat *sp = (og_splat *)malloc((size_t)(n > 0 ? n : 1) * sizeof(og_splat));
     og_pix_state *pix = (og_pix_state *)calloc((size_t)(npix > 0 ? npix : 1), sizeof(og_pix_state));
-    og_core_entry *core = (og_core_entry *)calloc((size_t)(npix * (prm->K > 0 ? prm->K : 1) + 1),
+    og_core_entry *core = (og_core_entry *)calloc((size_t)(npix * kcap + 1),
                                                   sizeof(og_core_entry));
     double *rec = (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double));
     int rc = 0;
     if (!sp || !pix || !core || !rec) rc = 2;
     if (!rc) rc = og_preprocess(g, cam, prm, sp);
     if (!rc) {
-        og_bwd_ctx c = {sp, n, cam, prm, *win, dl_dimg, pix, core, rec, 0, visibility};
+        og_bwd_ctx c = {sp, n, cam, prm, *win, dl_dimg, pix, core, rec, 0, visibility, kcap};
         og_parallel_for(npix, 4, og_bwd_pixel_task, &c);
         if (c.err) rc = 2;
         if (!rc) og_parallel_for(n, 8, og_bwd_gauss_task, &c);

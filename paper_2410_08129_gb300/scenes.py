@@ -101,6 +101,7 @@ class Params:
     alpha_max: float = 0.999
     bg: tuple = (0.0, 0.0, 0.0)
     no_tail: bool = False  # inference without the tail: core over the background
+    sorted_blend: bool = False  # mean-depth-sorted alpha blending ("w/o per-pixel HT")
 
 
 def _unit_quats(rng: np.random.Generator, n: int) -> np.ndarray:

@@ -74,6 +74,17 @@ def test_no_tail_gradient_matches_central_differences(K):
     assert n_cmp > 0.8 * (n_cmp + n_skip) and n_cmp > 300
 
 
+@pytest.mark.parametrize("boost", [0.0, 3.0])
+def test_sorted_blend_gradient_matches_central_differences(boost):
+    scene = scenes.small_box_scene(14, seed=230, sh_degree=1).astype(np.float64)
+    scene.log_scales += 0.7
+    scene.opacity_logits += boost
+    cam = scenes.fov_camera(scenes.look_at((0.2, -0.1, -0.3), (0.0, 0.1, 3.0)), 40, 30, 60.0)
+    prm = scenes.Params(K=4, bg=(0.3, 0.6, 0.2), sorted_blend=True)
+    n_cmp, n_skip = _fd_check(scene, cam, prm, (12, 8, 16, 14), seed=int(boost))
+    assert n_cmp > 0.7 * (n_cmp + n_skip) and n_cmp > 200
+
+
 def test_gradient_zero_where_alpha_clamped_and_colour_clamped():
     """No gradient flows to the opacity where alpha = alpha_max, nor to SH
     coefficients of a channel clamped at zero."""

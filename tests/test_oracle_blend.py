@@ -86,6 +86,64 @@ def test_no_tail_is_sorted_blend_of_the_core(K, tau_K):
     assert deep > 20  # pixels whose tail was dropped
 
 
+def _mean_depth_blend(frags, zmean, bg, tmin=1e-4):
+    """Eq. (2) over fragments in (mean depth, gid) order, stopping before the
+    fragment that would take the transmittance below tmin."""
+    C, T = np.zeros(3), 1.0
+    for z, gid, a, c in sorted(frags, key=lambda f: (zmean[f[1]], f[1])):
+        if T * (1.0 - a) < tmin:
+            break
+        C += a * T * np.asarray(c)
+        T *= 1.0 - a
+    return C + T * np.asarray(bg, np.float64), T
+
+
+@pytest.mark.parametrize("boost", [0.0, 8.0])
+def test_sorted_blend_uses_mean_depth_order_and_stops_early(boost):
+    """Tab. 3 "w/o per-pixel HT": fragments ordered by their Gaussian's
+    view-space mean depth (not the per-pixel depth), blended front to back;
+    with opaque splats (boost) the early termination is exercised."""
+    scene = _scene(16, 60 + int(boost))
+    scene.opacity_logits += boost
+    if boost:
+        scene.log_scales += 1.0  # overlapping opaque splats end the blending early
+    cam = scenes.identity_camera(20, 16, 20.0)
+    prm = scenes.Params(K=4, bg=(0.3, 0.1, 0.6), sorted_blend=True)
+    img, d = oracle.render(scene, cam, prm, diagnostics=True)
+    M = np.asarray(cam.world_to_cam)
+    zmean = (scene.means @ M[:3, :3].T + M[:3, 3])[:, 2]
+    stopped = reordered = 0
+    for j in range(cam.height):
+        for i in range(cam.width):
+            fr = _independent_fragments(scene, cam, prm, i + 0.5, j + 0.5)
+            ref, T = _mean_depth_blend(fr, zmean, prm.bg)
+            np.testing.assert_allclose(img[j, i], ref, rtol=1e-9, atol=1e-12)
+            assert d["T_core"][j, i] == pytest.approx(T, rel=1e-9, abs=1e-15)
+            used = int(d["n_core"][j, i])
+            stopped += used < len(fr)
+            by_pixel = [f[1] for f in sorted(fr, key=lambda f: (f[0], f[1]))]
+            by_mean = [f[1] for f in sorted(fr, key=lambda f: (zmean[f[1]], f[1]))]
+            reordered += by_pixel != by_mean
+    assert reordered > 0
+    if boost:
+        assert stopped > 0
+
+
+def test_sorted_blend_equals_hybrid_when_orders_agree():
+    """Isotropic splats spread in depth and translucent: the point of maximum
+    contribution on a ray is the centre's projection onto it, so here mean order =
+    per-pixel order and nothing stops early; with K >= |F| and tau_K = 0 both
+    blendings are Eq. (2)."""
+    scene = _scene(10, 70)
+    scene.means[:, 2] = 2.0 + 0.4 * np.arange(10)
+    scene.log_scales[:] = math.log(0.3)
+    scene.opacity_logits[:] = -1.0
+    cam = scenes.identity_camera(20, 16, 20.0)
+    a = oracle.render(scene, cam, scenes.Params(K=64, tau_K=0.0, bg=(0.2, 0.2, 0.2), sorted_blend=True))
+    b = oracle.render(scene, cam, scenes.Params(K=64, tau_K=0.0, bg=(0.2, 0.2, 0.2)))
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
 def test_k_zero_is_order_independent_blend():
     """K = 0 (full OIT): C = (1 - prod(1 - a)) sum(a c)/sum(a) + prod(1 - a) bg."""
     scene = _scene(14, 40)
