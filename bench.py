@@ -551,6 +551,28 @@ def main():
                "ms_per_step": notail_ms / args.steps, "workload": "the headline frame without the tail"}
     del nr, nimg
 
+    # ---- the variant without per-pixel hybrid transparency (Tab. 3) -------
+    sprm = scenes.Params(K=prm.K, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max,
+                         bg=prm.bg, sorted_blend=True)
+    sr = Renderer(cam, sprm, scene.n, launch=B.c_launch((16, 16), 1))
+    simg = sr.image_buffer()
+    sr.forward(g, image=simg, save=False, check=True)
+    for _ in range(max(args.warmup, 3)):
+        sr.forward(g, image=simg, save=False, check=False)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(args.steps):
+        sr.forward(g, image=simg, save=False, check=False)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    assert sr.status()[0] == B.HTGS_OK
+    sorted_ms = max_over_ranks(q0.elapsed_time(q1))
+    sorted_blend = {"value": job_throughput(args.steps, world, sorted_ms), "unit": UNIT,
+                    "ms_per_step": sorted_ms / args.steps,
+                    "workload": "the headline frame, mean-depth-sorted alpha blending with early termination"}
+    del sr, simg
+
     # ---- end to end through the C ABI with host buffers --------------------
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory()
             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
@@ -620,6 +642,31 @@ def main():
     assert st2 == B.HTGS_OK
     gfinite = all(bool(torch.isfinite(v).all()) for v in grads.values())
 
+    # the same training step with the variant without per-pixel HT (Tab. 3)
+    stprm = scenes.Params(K=tprm.K, tau_alpha=tprm.tau_alpha, tau_K=tprm.tau_K, alpha_max=tprm.alpha_max,
+                          bg=tprm.bg, sorted_blend=True)
+    str_ = Renderer(tcam, stprm, tscene.n, launch=B.c_launch((16, 16), 1))
+    starget = str_.forward(tt, save=False, check=True).clone()
+    str_.forward(tg, image=timg, save=True, check=True)
+
+    def sorted_train_step():
+        str_.forward(tg, image=timg, save=True, check=False)
+        B._check(B.htgs_l1_loss_grad(timg, starget, dl, loss), "htgs_l1_loss_grad")
+        str_.backward(tg, dl, grads=grads)
+
+    for _ in range(2):
+        sorted_train_step()
+    torch.cuda.synchronize()
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    for _ in range(max(3, n_train // 2)):
+        sorted_train_step()
+    u1.record(stream)
+    torch.cuda.synchronize()
+    assert str_.status()[0] == B.HTGS_OK
+    sorted_train_ms = max_over_ranks(u0.elapsed_time(u1)) / max(3, n_train // 2)
+    del str_, starget
+
     # ---- roofline of the dominant kernel (the forward blend) ---------------
     # Algorithmic FP32-pipe instructions of the quadratic-form evaluation:
     # 8 per pixel inside a tight bounding box (2 offsets, 5 FMA, 1 compare),
@@ -661,6 +708,8 @@ def main():
                     "grads_finite": gfinite},
         "filter3d": filtered,
         "no_tail": no_tail,
+        "sorted_blend": dict(sorted_blend, fwd_bwd={"value": job_throughput(1, world, sorted_train_ms),
+                                                     "unit": "steps/s", "ms_per_step": sorted_train_ms}),
         "batched_vs_plain": batched,
         "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,

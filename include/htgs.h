@@ -109,6 +109,11 @@ typedef struct {
     float bg[3];      /* background colour c_bg */
     int32_t no_tail;  /* 0: hybrid transparency (Eq. (15)); 1: inference without the tail
                          (Sec. 4.4 ablation): C = sum_core alpha_i T_i c_i + T_{K+1} c_bg */
+    int32_t sorted_blend; /* 1: the variant without per-pixel hybrid transparency (Tab. 3):
+                         the perspective-correct fragments of a pixel blended front to back
+                         (Eq. (2) plus background) in the order of their Gaussians' view-space
+                         mean depth (then index), stopping before the fragment that would take
+                         the transmittance below 1e-4; K, tau_K and no_tail are ignored */
 } htgs_params;
 
 /* Tuning knobs (none changes the result beyond float rounding order) and

@@ -50,7 +50,8 @@ class Camera(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("tau_alpha", ctypes.c_float), ("tau_K", ctypes.c_float),
-                ("alpha_max", ctypes.c_float), ("bg", ctypes.c_float * 3), ("no_tail", ctypes.c_int32)]
+                ("alpha_max", ctypes.c_float), ("bg", ctypes.c_float * 3), ("no_tail", ctypes.c_int32),
+                ("sorted_blend", ctypes.c_int32)]
 
 
 class Launch(ctypes.Structure):
@@ -143,6 +144,7 @@ def c_params(p) -> Params:
     for i in range(3):
         q.bg[i] = float(p.bg[i])
     q.no_tail = 1 if getattr(p, "no_tail", False) else 0
+    q.sorted_blend = 1 if getattr(p, "sorted_blend", False) else 0
     return q
 
 

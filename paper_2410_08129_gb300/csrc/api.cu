@@ -26,7 +26,10 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     // byte offsets inside the workspace
-    size_t status, stats, total, work, ghist, tickets, ranges, lookback, n_items, done, zero_end;
+    size_t status, stats, total, work, ghist, tickets, ranges, lookback, n_items, done;
+    size_t d_ghist, d_tickets, d_lookback, zero_end;  // depth sort (sorted blending)
+    size_t dkeys0, dvals0, dkeys1, dvals1, count_p, block_sums_p;
+    int sorted, n_dsort_blocks;
     size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, vis, end;
     int n_blocks, n_sort_blocks, passes, digit_bits, slots_cap, max_items;
     TileArgs tiles;
@@ -108,12 +111,25 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     L.slots_cap = (int)std::min<int64_t>(kMaxSlots, 2 * ((capacity + kMinChunk - 1) / kMinChunk) + 2);
     L.max_items = (int)(n_tiles + L.slots_cap);
     L.n_items = o; o = align_up(o + 4 * sizeof(uint32_t));
+    // Sorted blending: a 4-pass 32-bit radix sort of the records by mean depth.
+    L.sorted = prm->sorted_blend ? 1 : 0;
+    L.n_dsort_blocks = L.sorted ? (int)std::max<int64_t>(1, (n_rec + kSortTile - 1) / kSortTile) : 0;
+    L.d_ghist = o; o = align_up(o + (L.sorted ? kMaxPasses * kMaxRadix * sizeof(uint32_t) : 0));
+    L.d_tickets = o; o = align_up(o + (L.sorted ? kMaxPasses * sizeof(uint32_t) : 0));
+    L.d_lookback = o; o = align_up(o + (size_t)(L.sorted ? 4 : 0) * L.n_dsort_blocks * 256 * sizeof(unsigned long long));
     L.done = o; o = align_up(o + (size_t)L.slots_cap * sizeof(uint32_t));
     L.zero_end = o;
     L.rec = o; o = align_up(o + (size_t)n_rec * kRecF4 * sizeof(float4));
     L.rect = o; o = align_up(o + (size_t)n_rec * sizeof(uint2));
     L.count = o; o = align_up(o + (size_t)n_rec * sizeof(uint32_t));
     L.block_sums = o; o = align_up(o + (size_t)(L.n_blocks + 1) * sizeof(uint32_t));
+    const size_t dn = L.sorted ? (size_t)n_rec : 0;
+    L.dkeys0 = o; o = align_up(o + dn * sizeof(uint32_t));
+    L.dvals0 = o; o = align_up(o + dn * sizeof(uint32_t));
+    L.dkeys1 = o; o = align_up(o + dn * sizeof(uint32_t));
+    L.dvals1 = o; o = align_up(o + dn * sizeof(uint32_t));
+    L.count_p = o; o = align_up(o + dn * sizeof(uint32_t));
+    L.block_sums_p = o; o = align_up(o + (L.sorted ? (size_t)(L.n_blocks + 1) : 0) * sizeof(uint32_t));
     L.keys0 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.vals0 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
     L.keys1 = o; o = align_up(o + (size_t)capacity * sizeof(uint32_t));
@@ -147,6 +163,7 @@ void make_prm(const htgs_params *p, ParamArgs &a) {
     a.alpha_max = p->alpha_max;
     for (int i = 0; i < 3; ++i) a.bg[i] = p->bg[i];
     a.no_tail = p->no_tail ? 1 : 0;
+    a.sorted_blend = p->sorted_blend ? 1 : 0;
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -254,6 +271,11 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
         pre.count = at<uint32_t>(workspace, L.count);
         pre.block_sums = at<uint32_t>(workspace, L.block_sums);
         pre.stats = at<unsigned long long>(workspace, L.stats);
+        if (L.sorted) {
+            pre.dkey = at<uint32_t>(workspace, L.dkeys0);
+            pre.dval = at<uint32_t>(workspace, L.dvals0);
+            pre.dtotal = total + 1;
+        }
         preprocess_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(b, pre);
     }
     mark(launch, 1, s);
@@ -263,6 +285,25 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     bin.rect = at<uint2>(workspace, L.rect);
     bin.count = at<uint32_t>(workspace, L.count);
     bin.block_sums = at<uint32_t>(workspace, L.block_sums);
+    if (L.sorted && L.n_blocks > 0) {
+        // Records in order of view-space mean depth (stable, so equal depths
+        // keep the record order); emitting in that order makes every tile's
+        // list depth-ordered after the stable tile sort.
+        SortArgs ds{};
+        ds.capacity = L.n_rec; ds.total = total + 1; ds.passes = 4; ds.digit_bits = 8;
+        ds.keys[0] = at<uint32_t>(workspace, L.dkeys0); ds.vals[0] = at<uint32_t>(workspace, L.dvals0);
+        ds.keys[1] = at<uint32_t>(workspace, L.dkeys1); ds.vals[1] = at<uint32_t>(workspace, L.dvals1);
+        ds.ghist = at<uint32_t>(workspace, L.d_ghist);
+        ds.lookback = at<unsigned long long>(workspace, L.d_lookback);
+        ds.tickets = at<uint32_t>(workspace, L.d_tickets);
+        ds.n_sort_blocks = L.n_dsort_blocks; ds.status = status;
+        const int db = launch_sort(ds, s);
+        bin.perm = ds.vals[db];
+        bin.count = at<uint32_t>(workspace, L.count_p);
+        bin.block_sums = at<uint32_t>(workspace, L.block_sums_p);
+        launch_permute_counts(L.n_rec, bin.perm, at<uint32_t>(workspace, L.count), at<uint32_t>(workspace, L.count_p),
+                              at<uint32_t>(workspace, L.block_sums_p), s);
+    }
     bin.status = status; bin.capacity = capacity;
     bin.keys = at<uint32_t>(workspace, L.keys0);
     bin.vals = at<uint32_t>(workspace, L.vals0);
@@ -287,6 +328,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
 
     ScheduleArgs sc{};
     sc.total = total; sc.ranges = ra.ranges; sc.n_tiles = L.tiles.n_tiles;
+    sc.no_split = L.sorted;  // early termination does not merge across chunks
     sc.slots_cap = L.slots_cap;
     sc.items = at<int4>(workspace, L.items);
     sc.n_items = at<uint32_t>(workspace, L.n_items);
@@ -306,7 +348,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     const int ppt = (launch && launch->px_per_thread) ? launch->px_per_thread : 1;
     mark(launch, 3, s);
     mark(launch, 4, s);
-    if (!launch_blend_fwd(b, ba, ppt, s)) return HTGS_ERR_NOT_SUPPORTED;
+    if (L.sorted ? !launch_blend_sorted_fwd(b, ba, s) : !launch_blend_fwd(b, ba, ppt, s)) return HTGS_ERR_NOT_SUPPORTED;
     mark(launch, 5, s);
     return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
 }
@@ -379,7 +421,7 @@ htgs_status render_batch_backward(int n_views, const htgs_view *views, const htg
     for (int v = 0; v < n_views; ++v) want_vis = want_vis || views[v].grads->visibility;
     bb.vis = want_vis ? at<float>(workspace, L.vis) : nullptr;
     mark(launch, 0, s);
-    if (!launch_blend_bwd(b, bb, s)) return HTGS_ERR_NOT_SUPPORTED;
+    if (L.sorted ? !launch_blend_sorted_bwd(b, bb, s) : !launch_blend_bwd(b, bb, s)) return HTGS_ERR_NOT_SUPPORTED;
     mark(launch, 1, s);
     mark(launch, 2, s);
     if (L.n_blocks > 0) {

@@ -102,10 +102,12 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t c = i < a.n ? a.count[i] : 0u;
+    // The record emitted at position i (the identity unless an order is given).
+    const uint32_t rec = i < a.n ? (a.perm ? a.perm[i] : (uint32_t)i) : 0u;
     // The record's view: its tile numbering (row length and first global tile).
     uint32_t vtx = 0, vtoff = 0;
     if (c) {
-        const ViewDesc &V = b.v[view_of_record(b, i)];
+        const ViewDesc &V = b.v[view_of_record(b, rec)];
         vtx = (uint32_t)V.tiles_x;
         vtoff = (uint32_t)V.tile_off;
     }
@@ -121,8 +123,7 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
     uint32_t woff = 0;
     for (int w = 0; w < warp; ++w) woff += warp_tot[w];
     const uint64_t base = (uint64_t)a.block_sums[blockIdx.x] + woff;
-    const uint2 r = c ? a.rect[i] : make_uint2(0u, 0u);
-    const uint32_t gid0 = (uint32_t)((int64_t)blockIdx.x * kPreThreads + warp * 32);
+    const uint2 r = c ? a.rect[rec] : make_uint2(0u, 0u);
     const int iters = (int)((wtot + 31) / 32);
     for (int it = 0; it < iters; ++it) {
         const uint32_t j = (uint32_t)it * 32 + lane;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
         const uint32_t eL = __shfl_sync(kFull, excl, L);
         const uint32_t ltx = __shfl_sync(kFull, vtx, L);
         const uint32_t ltoff = __shfl_sync(kFull, vtoff, L);
+        const uint32_t lrec = __shfl_sync(kFull, rec, L);
         if (j < wtot) {
             const uint32_t rr = j - eL;
             const uint32_t tx0 = rx & 0xffffu, tx1 = rx >> 16;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
             const uint64_t pos = base + j;
             if (pos < (uint64_t)a.capacity) {
                 a.keys[pos] = ltoff + ty * ltx + tx;
-                a.vals[pos] = gid0 + (uint32_t)L;
+                a.vals[pos] = lrec;
             }
         }
     }
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a)
     const uint64_t need = (2 * total + (uint64_t)a.slots_cap - 1) / (uint64_t)max(a.slots_cap, 1);
     if (chunk < need) chunk = need;
     auto parts = [&](uint32_t cnt) -> int {
-        return cnt > chunk ? (int)((cnt + chunk - 1) / chunk) : 1;
+        return (!a.no_split && cnt > chunk) ? (int)((cnt + chunk - 1) / chunk) : 1;
     };
     for (int b = tid; b < kSchedBuckets; b += kSchedThreads) s_cnt[b] = 0;
     if (tid == 0) s_slots = 0;
@@ -411,7 +413,35 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a)
     }
 }
 
+// Counts in emission order and their per-block sums.
+__global__ void __launch_bounds__(kPreThreads) permute_counts_kernel(long long n, const uint32_t *perm,
+                                                                     const uint32_t *count, uint32_t *count_p,
+                                                                     uint32_t *block_sums) {
+    __shared__ uint32_t warp_sums[kPreThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
+    uint32_t c = 0;
+    if (i < n) {
+        const uint32_t r = perm[i];
+        c = r < (uint64_t)n ? count[r] : 0u;
+        count_p[i] = c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kPreThreads / 32; ++w) tot += warp_sums[w];
+        block_sums[blockIdx.x] = tot;
+    }
+}
+
 } // namespace
+
+void launch_permute_counts(long long n, const uint32_t *perm, const uint32_t *count, uint32_t *count_p,
+                           uint32_t *block_sums, cudaStream_t s) {
+    const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
+    if (blocks > 0) permute_counts_kernel<<<blocks, kPreThreads, 0, s>>>(n, perm, count, count_p, block_sums);
+}
 
 void launch_schedule(const ScheduleArgs &a, cudaStream_t s) {
     schedule_kernel<<<1, kSchedThreads, 0, s>>>(a);

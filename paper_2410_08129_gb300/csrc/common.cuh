@@ -26,7 +26,11 @@ struct ParamArgs {
     float tau_alpha, tau_K, alpha_max;
     float bg[3];
     int no_tail;  // 1: the tail is omitted (core over the background)
+    int sorted_blend;  // 1: mean-depth-sorted alpha blending with early termination
 };
+
+// Sorted blending stops before the fragment that would take T below this.
+constexpr float kSortedTmin = 1e-4f;
 
 struct TileArgs {
     int tile_w, tile_h;

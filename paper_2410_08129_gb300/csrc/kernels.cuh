@@ -79,6 +79,9 @@ __device__ __forceinline__ int view_of_tile(const Batch &b, int t) {
 struct PreArgs {
     ParamArgs prm;
     TileArgs tiles;        // tile shape (counts per view are in the batch)
+    uint32_t *dkey;        // sorted blending: n_rec mean-depth keys (float bits), or nullptr
+    uint32_t *dval;        // sorted blending: n_rec record indices
+    uint32_t *dtotal;      // sorted blending: receives n_rec (the depth sort's length)
     float4 *rec;           // n_rec * kRecF4
     uint2 *rect;           // n_rec: (tx0 | tx1 << 16, ty0 | ty1 << 16), view-local tiles
     uint32_t *count;       // n_rec
@@ -98,8 +101,9 @@ struct PreBwdArgs {
 struct BinArgs {
     long long n;           // records
     int n_blocks;          // ceil(n / kPreThreads)
+    const uint32_t *perm;  // emission order of the records (position -> record), or nullptr
     const uint2 *rect;
-    const uint32_t *count;
+    const uint32_t *count; // per position (permuted when perm is set)
     uint32_t *block_sums;  // in: per-block sums; out: exclusive block offsets
     int *status;
     int64_t capacity;
@@ -132,6 +136,7 @@ struct ScheduleArgs {
     const uint32_t *total;
     const uint2 *ranges;
     int n_tiles;
+    int no_split;          // 1: one item per tile (sorted blending)
     int slots_cap;         // partial-state slots available
     int4 *items;           // n_tiles + slots_cap
     uint32_t *n_items;
@@ -193,6 +198,9 @@ void launch_emit(const Batch &b, const BinArgs &a, cudaStream_t s);
 // Returns the buffer index (0 or 1) holding the result.
 int launch_sort(const SortArgs &a, cudaStream_t s);
 void launch_ranges(RangeArgs a, cudaStream_t s);
+// Counts in the order perm gives and their per-block sums (for the scan).
+void launch_permute_counts(long long n, const uint32_t *perm, const uint32_t *count, uint32_t *count_p,
+                           uint32_t *block_sums, cudaStream_t s);
 // Blend work items from the tile ranges (one CTA).
 void launch_schedule(const ScheduleArgs &a, cudaStream_t s);
 
@@ -200,6 +208,9 @@ void launch_schedule(const ScheduleArgs &a, cudaStream_t s);
 // when (K, tile shape, px/thread) has no compiled instance.
 bool launch_blend_fwd(const Batch &b, const BlendFwdArgs &a, int px_per_thread, cudaStream_t s);
 bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s);
+// The same for mean-depth-sorted blending (one item per tile).
+bool launch_blend_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s);
+bool launch_blend_sorted_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s);
 
 // CTAs per SM the persistent kernels are launched with (occupancy query).
 int persistent_grid(const void *kernel, int threads, size_t dyn_smem, int items);

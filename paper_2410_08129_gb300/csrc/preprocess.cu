@@ -352,6 +352,13 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
         for (int k = 0; k < kRecF4; ++k) slab[lane * kRecF4 + (k ^ (lane & 7))] = rec[k];
         a.rect[i] = rect;
         a.count[i] = count;
+        // Sorted blending: key = view-space mean depth (positive, so its float
+        // bits order like the depth); records that emit nothing go last.
+        if (a.dkey) {
+            a.dkey[i] = count ? __float_as_uint(S.mu[2]) : 0xffffffffu;
+            a.dval[i] = (uint32_t)i;
+            if (i == 0) *a.dtotal = (uint32_t)b.n_rec;
+        }
     }
     // The warp's 32 records are contiguous in global memory: store them as
     // 4 KB of consecutive float4s.
