@@ -472,10 +472,22 @@ def main():
     scene, cam, prm = scenes.config2(seed=1 + rank)
     cam = cam.rounded()
     g = GaussianTensors.from_scene(scene)
+    # Launch shape (tile, pixels per thread, staging batch) from the autotuner.
+    from paper_2410_08129_gb300.autotune import autotune
+
+    def fwd_step_for(launch_):
+        rr = Renderer(cam, prm, scene.n, launch=launch_)
+        im = rr.image_buffer()
+        rr.forward(g, image=im, save=False, check=True)
+        return lambda: rr.forward(g, image=im, save=False, check=False)
+
+    best_fwd, tune_fwd = autotune(fwd_step_for, warmup=2, repeats=5)
+    torch.cuda.empty_cache()
+    fwd_shape = ((best_fwd.tile_w, best_fwd.tile_h), best_fwd.px_per_thread, best_fwd.smem_batch)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     for e in ev:
         e.record(stream)
-    launch = B.c_launch((16, 16), 1, 0, ev)
+    launch = B.c_launch(fwd_shape[0], fwd_shape[1], 0, ev, smem_batch=fwd_shape[2])
     r = Renderer(cam, prm, scene.n, launch=launch)
     image = r.image_buffer()
     r.forward(g, image=image, save=False, check=True)       # sizes the instance capacity
@@ -510,7 +522,7 @@ def main():
     # ---- the same frame with the 3D smoothing filter (Sec. 4.2) -----------
     fscene = scene.with_filter(scenes.filter_variance_from_cameras(scene.means, [cam]))
     fg = GaussianTensors.from_scene(fscene)
-    fr = Renderer(cam, prm, scene.n, launch=B.c_launch((16, 16), 1))
+    fr = Renderer(cam, prm, scene.n, launch=B.c_launch(*fwd_shape[:2], smem_batch=fwd_shape[2]))
     fimg = fr.image_buffer()
     fr.forward(fg, image=fimg, save=False, check=True)
     for _ in range(max(args.warmup, 3)):
@@ -533,7 +545,7 @@ def main():
     # ---- the same frame rendered without the tail (inference variant) ------
     nprm = scenes.Params(K=prm.K, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max,
                          bg=prm.bg, no_tail=True)
-    nr = Renderer(cam, nprm, scene.n, launch=B.c_launch((16, 16), 1))
+    nr = Renderer(cam, nprm, scene.n, launch=B.c_launch(*fwd_shape[:2], smem_batch=fwd_shape[2]))
     nimg = nr.image_buffer()
     nr.forward(g, image=nimg, save=False, check=True)
     for _ in range(max(args.warmup, 3)):
@@ -554,7 +566,7 @@ def main():
     # ---- the variant without per-pixel hybrid transparency (Tab. 3) -------
     sprm = scenes.Params(K=prm.K, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max,
                          bg=prm.bg, sorted_blend=True)
-    sr = Renderer(cam, sprm, scene.n, launch=B.c_launch((16, 16), 1))
+    sr = Renderer(cam, sprm, scene.n, launch=B.c_launch(*fwd_shape[:2], smem_batch=fwd_shape[2]))
     simg = sr.image_buffer()
     sr.forward(g, image=simg, save=False, check=True)
     for _ in range(max(args.warmup, 3)):
@@ -604,10 +616,29 @@ def main():
     tcam = tcam.rounded()
     tg = GaussianTensors.from_scene(tscene)
     tt = GaussianTensors.from_scene(ttarget)
+    def train_step_for(launch_):
+        rr = Renderer(tcam, tprm, tscene.n, launch=launch_)
+        tgt = rr.forward(tt, save=False, check=True).clone()
+        im = rr.image_buffer()
+        dl_ = torch.empty_like(im)
+        loss_ = torch.zeros(1, dtype=torch.float32, device="cuda")
+        grads_ = {k: torch.empty_like(getattr(tg, k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        rr.forward(tg, image=im, save=True, check=True)
+
+        def step():
+            rr.forward(tg, image=im, save=True, check=False)
+            B._check(B.htgs_l1_loss_grad(im, tgt, dl_, loss_), "htgs_l1_loss_grad")
+            rr.backward(tg, dl_, grads=grads_)
+        return step
+
+    best_train, tune_train = autotune(train_step_for, warmup=1, repeats=3)
+    torch.cuda.empty_cache()
+    train_shape = ((best_train.tile_w, best_train.tile_h), best_train.px_per_thread, best_train.smem_batch)
     bev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     for e in bev:
         e.record(stream)
-    tr = Renderer(tcam, tprm, tscene.n, launch=B.c_launch((16, 16), 2, 0, bev))
+    tr = Renderer(tcam, tprm, tscene.n, launch=B.c_launch(train_shape[0], train_shape[1], 0, bev,
+                                                          smem_batch=train_shape[2]))
     target = tr.forward(tt, save=False, check=True).clone()
     timg = tr.image_buffer()
     dl = torch.empty_like(timg)
@@ -645,7 +676,8 @@ def main():
     # the same training step with the variant without per-pixel HT (Tab. 3)
     stprm = scenes.Params(K=tprm.K, tau_alpha=tprm.tau_alpha, tau_K=tprm.tau_K, alpha_max=tprm.alpha_max,
                           bg=tprm.bg, sorted_blend=True)
-    str_ = Renderer(tcam, stprm, tscene.n, launch=B.c_launch((16, 16), 1))
+    str_ = Renderer(tcam, stprm, tscene.n,
+                    launch=B.c_launch(train_shape[0], train_shape[1], smem_batch=train_shape[2]))
     starget = str_.forward(tt, save=False, check=True).clone()
     str_.forward(tg, image=timg, save=True, check=True)
 
@@ -697,13 +729,19 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": cam.width, "height": cam.height,
-                   "K": K, "tile": "16x16", "px_per_thread": 1, "parallelism": f"replicas{world}",
+                   "K": K, "tile": f"{fwd_shape[0][0]}x{fwd_shape[0][1]}", "px_per_thread": fwd_shape[1],
+                   "smem_batch": fwd_shape[2], "parallelism": f"replicas{world}",
+                   "autotune_ms": {f"{t[0]}x{t[1]}/ppt{pp}/b{bb}": round(v, 4) for (t, pp, bb), v in tune_fwd.items()},
                    "l2": "inputs larger than L2 (236 MB of Gaussian parameters per frame)"},
         "phases_ms": {"preprocess": float(np.mean(pre_ms)), "binning_sort": float(np.mean(bin_ms)),
                       "blend": float(np.mean(blend_ms))},
         "instances": inst, "counters": counters,
         "fwd_bwd": {"value": job_throughput(1, world, train_ms), "unit": "steps/s", "ms_per_step": train_ms,
                     "workload": "500k Gaussians (box distribution), 1200x800, K=8: render + L1 + backward",
+                    "launch": {"tile": f"{train_shape[0][0]}x{train_shape[0][1]}", "px_per_thread": train_shape[1],
+                               "smem_batch": train_shape[2],
+                               "autotune_ms": {f"{t[0]}x{t[1]}/ppt{pp}/b{bb}": round(v, 2)
+                                               for (t, pp, bb), v in tune_train.items()}},
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
                     "grads_finite": gfinite},
         "filter3d": filtered,
