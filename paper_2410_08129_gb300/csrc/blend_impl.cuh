@@ -1,13 +1,13 @@
 // blend_impl.cuh -- per-pixel ray-splat evaluation and hybrid-transparency
-// blending (arXiv 2410.08129, Sec. 3.2 Eq. (13), Sec. 3.3 Eq. (14)-(16)) and
-// its adjoint.
+// blending (arXiv 2410.08129, Sec. 3.2 Eq. (13), Sec. 3.3 Eq. (14)-(16)):
+// the forward kernel and the evaluation helpers its adjoints share.
 //
 // Forward: one CTA per tile of TW x TH pixels; each warp owns an 8 x (4 PPT)
 // pixel footprint and each lane PPT vertically adjacent pixels. The tile's
 // instance list (gid ascending, no depth order) is staged through shared
-// memory in batches of records, double-buffered with cp.async so that the
-// gather of the next batch overlaps the evaluation of the current one. A
-// warp first culls a batch against its footprint (one bounding-box test per
+// memory in batches of records, three buffers deep with cp.async so that the
+// gathers of the next two batches overlap the evaluation of the current one.
+// A warp first culls a batch against its footprint (one bounding-box test per
 // lane and record, one ballot per 32 records) and evaluates only the records
 // that touch it. For each pixel one packed FP32x2 evaluation gives the pair
 // (Q, D) of a record: Q >= 0 decides rho^2 <= rho_c and D gives alpha. Kept
@@ -16,14 +16,6 @@
 // alpha >= tau_K, a K-core of (depth, gid) pairs held in registers in
 // ascending order. The tail is "all fragments minus the core": its sums are
 // recovered in the epilogue, so an evicted core entry needs no colour.
-//
-// Adjoint: one CTA per tile. The per-pixel adjoint state (the shared tail
-// partials of Sec. 3.3 and the core's dL/dalpha, dL/dc) is built once in
-// shared memory; then every warp independently pulls whole records from a
-// shared counter (prefetching the next with cp.async into a private slot)
-// and its lanes walk the pixels of the record's bounding box inside the
-// tile, so the 16 gradient accumulators of a record are reduced once per
-// (record, tile) and no block-wide barrier is needed.
 #pragma once
 
 #include "common.cuh"
@@ -36,8 +28,6 @@ namespace htgs {
 __host__ __device__ inline size_t fwd_smem_bytes(int B) {
     return (size_t)3 * B * (kRecF4 * sizeof(float4) + sizeof(uint32_t));
 }
-
-constexpr int kBwdThreads = 256;
 
 // Alpha of one record at a pixel from its (Q, D) pair, evaluated identically
 // in the main loop, the epilogue and the adjoint.
@@ -380,12 +370,7 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint (K7). The derivative of the colour with respect to every tail
-// fragment uses only per-pixel constants (Sec. 3.3): with u = g (T_c - P)/A,
-// k0 = -u.c_tail and k1 = P g.(c_tail - bg), dL/dalpha_j = u.c_j + k0 +
-// k1/(1 - alpha_j) and dL/dc_j = u alpha_j. Core fragment r (depth order)
-// has dL/dalpha_r = T_r g.(c_r - G_r) and dL/dc_r = g alpha_r T_r, with G_r
-// the colour seen behind r.
+// Warp reduction shared by the adjoint kernels.
 // ---------------------------------------------------------------------------
 
 // Sums 16 per-lane values over the warp; afterwards lane 8q (q = 0..3) holds
@@ -409,300 +394,6 @@ __device__ __forceinline__ void warp_reduce16_to4(float (&v)[16], int lane) {
     for (int o = 4; o > 0; o >>= 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-}
-
-// Dynamic shared memory of the adjoint for a TP-pixel tile and core size K.
-__host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
-    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float) + sizeof(float));
-}
-
-template <int TW, int TH, bool NOTAIL, bool VIS>
-__global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
-    constexpr int TP = TW * TH;
-    constexpr int NW = kBwdThreads / 32;
-    extern __shared__ float4 smem[];
-    __shared__ float4 s_wrec[NW][2][kRecF4];  // per-warp double-buffered record
-    __shared__ uint32_t s_wgid[NW][2];
-    __shared__ uint32_t s_next;
-    __shared__ int s_item;
-    __shared__ float s_wzmax[NW];
-    __shared__ int s_wopen[NW];
-    const int K = a.prm.K;
-    const int n_items = min((int)*a.n_items, a.max_items);
-    float4 *s_pa = smem;                 // g.xyz, k0
-    float4 *s_pb = s_pa + TP;            // u.xyz, k1
-    float4 *s_pc = s_pb + TP;            // last core depth, last core gid, mode, -
-    uint32_t *s_cg = reinterpret_cast<uint32_t *>(s_pc + TP);        // [K][TP] core gids
-    float *s_cw = reinterpret_cast<float *>(s_cg + (size_t)K * TP);  // [K][TP] dL/dalpha_r
-    float *s_cv = s_cw + (size_t)K * TP;                             // [K][TP] alpha_r T_r
-    float *s_wt = s_cv + (size_t)K * TP;                             // [TP] T_core (1 - T_tail) / A
-    if (a.status[kStError] != 0) return;
-
-    // Persistent CTA: take (view, tile, chunk) items from the shared queue.
-    // The adjoint of a chunk needs only the saved per-pixel state, so the
-    // chunks of a split tile are independent.
-    for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= n_items) break;
-    const int4 work = a.items[item];
-    const int tile = work.x;
-    if (!item_ok(work, bt.total_tiles, a.max_items)) continue;  // (the adjoint uses no slots)
-    const ViewDesc &view = bt.v[view_of_tile(bt, tile)];
-    const int local = tile - view.tile_off;
-    const int tx = local % view.tiles_x, ty = local / view.tiles_x;
-    const int width = view.cam.width, height = view.cam.height;
-    const float *const saved = view.saved;
-    const float *const dl_dimg = view.dl_dimg;
-    const long long n_rec = bt.n_rec;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = tx * TW, y0 = ty * TH;
-    const int x1 = min(x0 + TW, width) - 1, y1 = min(y0 + TH, height) - 1;
-    const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
-    const float bg0 = a.prm.bg[0], bg1 = a.prm.bg[1], bg2 = a.prm.bg[2];
-    const size_t npix = (size_t)width * height;
-    const uint2 range = chunk_range(a.ranges[tile], work.y, work.z);
-
-    // Phase A: per-pixel adjoint state. Also, over the tile's pixels: the
-    // deepest last core entry of full cores and whether a core is not full
-    // (there every candidate belongs to it).
-    float zmax_l = -INFINITY;
-    bool open_l = false;
-    for (int p = tid; p < TP; p += kBwdThreads) {
-        const int x = x0 + p % TW, y = y0 + p / TW;
-        const bool inside = x < width && y < height;
-        const size_t pix = inside ? (size_t)y * width + x : 0;
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        int n_core = 0;
-        float Tc = 1.f, Pc = 1.f, At = 0.f, ct0 = 0.f, ct1 = 0.f, ct2 = 0.f;
-        if (inside) {
-            g0 = dl_dimg[pix * 3 + 0];
-            g1 = dl_dimg[pix * 3 + 1];
-            g2 = dl_dimg[pix * 3 + 2];
-            n_core = min(max(__float_as_int(saved[0 * npix + pix]), 0), K);
-            Tc = saved[1 * npix + pix];
-            Pc = saved[2 * npix + pix];
-            At = saved[3 * npix + pix];
-            ct0 = saved[4 * npix + pix];
-            ct1 = saved[5 * npix + pix];
-            ct2 = saved[6 * npix + pix];
-        }
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f, k0 = 0.f, k1 = 0.f;
-        // A tail fragment's blending weight is alpha_j T_core (1 - T_tail) / A.
-        s_wt[p] = At > 0.f ? __fdividef(Tc - Pc, At) : 0.f;
-        if (At > 0.f) {
-            const float s = __fdividef(Tc - Pc, At);
-            u0 = g0 * s; u1 = g1 * s; u2 = g2 * s;
-            k0 = -(u0 * ct0 + u1 * ct1 + u2 * ct2);
-            k1 = Pc * (g0 * (ct0 - bg0) + g1 * (ct1 - bg1) + g2 * (ct2 - bg2));
-        }
-        s_pa[p] = make_float4(g0, g1, g2, k0);
-        s_pb[p] = make_float4(u0, u1, u2, k1);
-        // Colour seen behind the core: (1 - T_tail) c_tail + T_tail bg, T_tail = P / T_c.
-        const float Tt = (At > 0.f && Tc > 0.f) ? fminf(__fdividef(Pc, Tc), 1.f) : 1.f;
-        float G0 = (1.f - Tt) * ct0 + Tt * bg0, G1 = (1.f - Tt) * ct1 + Tt * bg1, G2 = (1.f - Tt) * ct2 + Tt * bg2;
-        float lastz = INFINITY;
-        uint32_t lastg = 0xffffffffu;
-        // Back to front: u_r = g.(c_r - G_r) into s_cw, alpha_r into s_cv.
-        for (int r = n_core - 1; r >= 0; --r) {
-            const uint32_t gid = __float_as_uint(saved[(size_t)(7 + r) * npix + pix]);
-            float ur = 0.f, al = 0.f;
-            if ((long long)gid < n_rec) {
-                const float4 *rr = a.rec + (size_t)gid * kRecF4;
-                const float4 c0 = rr[0], c1 = rr[1], c2 = rr[2], c4 = rr[4], c5 = rr[5];
-                const float ex = __fsub_rn((float)x + 0.5f, c4.z), ey = __fsub_rn((float)y + 0.5f, c4.w);
-                FragEval f;
-                frag_alpha(quad_eval2(c0, c1, c2, ex, ey), tau_alpha, alpha_max, f);
-                al = f.alpha;
-                ur = g0 * (c5.x - G0) + g1 * (c5.y - G1) + g2 * (c5.z - G2);
-                G0 = al * c5.x + (1.f - al) * G0;
-                G1 = al * c5.y + (1.f - al) * G1;
-                G2 = al * c5.z + (1.f - al) * G2;
-                if (r == K - 1) {
-                    lastz = frag_depth(rr[3], c4, ex, ey, f.rD);
-                    lastg = gid;
-                }
-            }
-            s_cg[(size_t)r * TP + p] = gid;
-            s_cw[(size_t)r * TP + p] = ur;
-            s_cv[(size_t)r * TP + p] = al;
-        }
-        // Front to back: T_r; dL/dalpha_r = T_r u_r, dL/dc_r = g alpha_r T_r.
-        float T = 1.f;
-        for (int r = 0; r < n_core; ++r) {
-            const float al = s_cv[(size_t)r * TP + p];
-            s_cw[(size_t)r * TP + p] *= T;
-            s_cv[(size_t)r * TP + p] = al * T;
-            T = __fmaf_rn(-T, al, T);
-        }
-        // mode 0: no core (K = 0); 1: every candidate is in the core; 2: compare with the last entry.
-        const int mode = K == 0 ? 0 : (n_core < K ? 1 : 2);
-        s_pc[p] = make_float4(lastz, __uint_as_float(lastg), __int_as_float(mode), 0.f);
-        if (inside && mode == 1) open_l = true;
-        if (inside && mode == 2) zmax_l = fmaxf(zmax_l, lastz);
-    }
-    for (int o = 16; o > 0; o >>= 1) zmax_l = fmaxf(zmax_l, __shfl_xor_sync(0xffffffffu, zmax_l, o));
-    open_l = __any_sync(0xffffffffu, open_l);
-    if (lane == 0) {
-        s_wzmax[warp] = zmax_l;
-        s_wopen[warp] = open_l ? 1 : 0;
-    }
-    if (tid == 0) s_next = range.x;
-    __syncthreads();
-    // A record whose depths all exceed the deepest last core entry belongs
-    // to no pixel's core in this tile (unless some core is not full).
-    float tile_zmax = -INFINITY;
-    int tile_open = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        tile_zmax = fmaxf(tile_zmax, s_wzmax[w]);
-        tile_open |= s_wopen[w];
-    }
-
-    // Phase B: warps pull records; lanes walk the record's box in the tile.
-    auto grab = [&]() -> uint32_t {
-        uint32_t j = 0;
-        if (lane == 0) j = atomicAdd(&s_next, 1u);
-        return __shfl_sync(0xffffffffu, j, 0);
-    };
-    auto issue = [&](uint32_t j, int slot) {
-        if (lane < kRecF4) {
-            const uint32_t gid = a.vals[j];
-            cp_async16(&s_wrec[warp][slot][lane], a.rec + (size_t)gid * kRecF4 + lane);
-            if (lane == 0) s_wgid[warp][slot] = gid;
-        }
-        cp_async_commit();
-    };
-    constexpr float kLn2 = 0.69314718055994531f;
-    uint32_t j = grab();
-    int slot = 0;
-    if (j < range.y) issue(j, 0);
-    while (j < range.y) {
-        const uint32_t jn = grab();
-        if (jn < range.y) {
-            issue(jn, slot ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncwarp();
-        const float4 *rec = s_wrec[warp][slot];
-        const uint32_t gid = s_wgid[warp][slot];
-        const float4 c6 = rec[6];
-        const int ix0 = (int)fmaxf(ceilf(c6.x - 0.5f), (float)x0);
-        const int ix1 = (int)fminf(floorf(c6.y - 0.5f), (float)x1);
-        const int iy0 = (int)fmaxf(ceilf(c6.z - 0.5f), (float)y0);
-        const int iy1 = (int)fminf(floorf(c6.w - 0.5f), (float)y1);
-        if (ix0 <= ix1 && iy0 <= iy1) {
-            const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c3 = rec[3], c4 = rec[4], c5 = rec[5];
-            const float zlo = rec[7].x;
-            const bool may_core = tile_open || !(zlo > tile_zmax);
-            float2 acc[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
-            float gaa = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
-            float wmax = 0.f;  // largest blending weight of the record in this tile
-            bool touched = false;
-            const int lx = lane & 7, ly = lane >> 3;
-            for (int by = iy0; by <= iy1; by += 4) {
-                const int y = by + ly;
-                const float dy = __fsub_rn((float)y + 0.5f, c4.w);
-                const int prow = (y - y0) * TW - x0;
-                for (int bx = ix0; bx <= ix1; bx += 8) {
-                    const int x = bx + lx;
-                    if (x > ix1 || y > iy1) continue;
-                    const float dx = __fsub_rn((float)x + 0.5f, c4.z);
-                    FragEval f;
-                    if (!frag_alpha(quad_eval2(c0, c1, c2, dx, dy), tau_alpha, alpha_max, f)) continue;
-                    const int p = prow + x;
-                    const float al = f.alpha;
-                    bool in_core = false;
-                    if (may_core && al >= tau_K) {
-                        const float4 PC = s_pc[p];
-                        const int mode = __float_as_int(PC.z);
-                        if (mode == 1) {
-                            in_core = true;
-                        } else if (mode == 2 && !(zlo > PC.x)) {
-                            // (depths of this splat are >= zlo, so zlo > last
-                            // core depth means the fragment is not in the core)
-                            const float z = frag_depth(c3, c4, dx, dy, f.rD);
-                            in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
-                        }
-                    }
-                    if (NOTAIL && !in_core) continue;  // an omitted tail has no gradient
-                    float dA, dc0, dc1, dc2;
-                    if (in_core) {
-                        const float4 PA = s_pa[p];
-                        float w = 0.f, s = 0.f;
-                        for (int r = 0; r < K; ++r)
-                            if (s_cg[(size_t)r * TP + p] == gid) {
-                                w = s_cw[(size_t)r * TP + p];
-                                s = s_cv[(size_t)r * TP + p];
-                                break;
-                            }
-                        dA = w;
-                        dc0 = PA.x * s; dc1 = PA.y * s; dc2 = PA.z * s;
-                        if (VIS) wmax = fmaxf(wmax, s);
-                    } else {
-                        const float4 PB = s_pb[p];
-                        const float k0 = s_pa[p].w;
-                        const float inv = rcp_approx(1.f - al);
-                        dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + k0 + PB.w * inv;
-                        dc0 = PB.x * al; dc1 = PB.y * al; dc2 = PB.z * al;
-                        if (VIS) wmax = fmaxf(wmax, al * s_wt[p]);
-                    }
-                    touched = true;
-                    gc0 += dc0; gc1 += dc1; gc2 += dc2;
-                    if (f.araw < alpha_max) {
-                        // With g = alpha dL/dalpha: dL/drho^2 = -g/2, and as
-                        // rho^2 = N / D = rho_c - 2 ln2 t, dL/dN = -e/2 and
-                        // dL/dD = e rho^2 / 2 = (rho_c e - 2 ln2 e t) / 2 for
-                        // e = g / D. The pixel adds the moments of (e, e t);
-                        // the (record, tile) sums become dL/dN and dL/dD once,
-                        // after the warp reduction.
-                        const float g = dA * al;
-                        gaa += g;
-                        const float e = g * f.rD;
-                        const float2 et = make_float2(e, e * f.t);
-                        const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
-                        const float2 ex = fmul2(et, X), ey = fmul2(et, Y);
-                        acc[0] = fadd2(acc[0], et);
-                        acc[1] = fadd2(acc[1], ex);
-                        acc[2] = fadd2(acc[2], ey);
-                        acc[3] = ffma2(ex, X, acc[3]);
-                        acc[4] = ffma2(ex, Y, acc[4]);
-                        acc[5] = ffma2(ey, Y, acc[5]);
-                    }
-                }
-            }
-            if (VIS) {
-                for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-                // Non-negative floats order like their bit patterns.
-                if (lane == 0 && wmax > 0.f) atomicMax(reinterpret_cast<int *>(a.vis) + gid, __float_as_int(wmax));
-            }
-            if (__any_sync(0xffffffffu, touched)) {
-                float v[16] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y,
-                               acc[4].x, acc[4].y, acc[5].x, acc[5].y, gaa, gc0, gc1, gc2};
-                warp_reduce16_to4(v, lane);
-                if ((lane & 7) == 0) {
-                    if (lane < 24) {  // two (sum e m, sum e t m) pairs -> (dL/dN_m, dL/dD_m)
-                        const float rc = c5.w;
-                        const float n0 = -0.5f * v[0], d0 = 0.5f * rc * v[0] - kLn2 * v[1];
-                        const float n1 = -0.5f * v[2], d1 = 0.5f * rc * v[2] - kLn2 * v[3];
-                        v[0] = n0; v[1] = d0; v[2] = n1; v[3] = d1;
-                    }
-                    red_add_v4(a.acc + (size_t)gid * 16 + (lane >> 3) * 4, v[0], v[1], v[2], v[3]);
-                }
-            }
-        }
-        __syncwarp();
-        slot ^= 1;
-        j = jn;
-    }
-    __syncthreads();  // the next item rebuilds the per-pixel state
-    } // next item
 }
 
 // ---------------------------------------------------------------------------
