@@ -125,7 +125,7 @@ typedef struct {
  *           around the blend; htgs_render_backward records [0]/[1] around
  *           the blend adjoint and [2]/[3] around the preprocess adjoint. */
 typedef struct {
-    int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 16x8 or 8x8 */
+    int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 32x16, 16x8 or 8x8 */
     int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4
                                  (1 when params.no_tail is set) */
     int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */

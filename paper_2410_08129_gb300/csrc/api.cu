@@ -42,7 +42,7 @@ bool tile_shape(const htgs_launch *launch, TileArgs &t) {
     t.depth_bits = launch ? launch->depth_bits : 0;
     t.batch = (launch && launch->smem_batch) ? launch->smem_batch : 128;
     const bool shape_ok = (t.tile_w == 16 && t.tile_h == 16) || (t.tile_w == 16 && t.tile_h == 8) ||
-                          (t.tile_w == 8 && t.tile_h == 8);
+                          (t.tile_w == 8 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 16);
     const bool batch_ok = t.batch == 32 || t.batch == 64 || t.batch == 128;
     return shape_ok && batch_ok && t.depth_bits == 0;
 }

@@ -9,6 +9,7 @@
 // accumulators of a record are reduced once per (record, tile) and no
 // block-wide barrier is needed.
 #include "blend_impl.cuh"
+#include "warp_reduce.cuh"
 
 namespace htgs {
 
@@ -25,7 +26,7 @@ constexpr int kBwdThreads = 256;
 
 // Dynamic shared memory of the adjoint for a TP-pixel tile and core size K.
 __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
-    return (size_t)TP * (3 * sizeof(float4) + (size_t)K * 3 * sizeof(float) + sizeof(float));
+    return (size_t)TP * (2 * sizeof(float4) + sizeof(float2) + (size_t)K * 3 * sizeof(float) + sizeof(float));
 }
 
 template <int TW, int TH, bool NOTAIL, bool VIS>
@@ -43,7 +44,9 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
     const int n_items = min((int)*a.n_items, a.max_items);
     float4 *s_pa = smem;                 // g.xyz, k0
     float4 *s_pb = s_pa + TP;            // u.xyz, k1
-    float4 *s_pc = s_pb + TP;            // last core depth, last core gid, mode, -
+    // Last core entry (depth, gid) of a full core; depth +inf where the core
+    // is not full (every candidate there belongs to it).
+    float2 *s_pc = reinterpret_cast<float2 *>(s_pb + TP);
     uint32_t *s_cg = reinterpret_cast<uint32_t *>(s_pc + TP);        // [K][TP] core gids
     float *s_cw = reinterpret_cast<float *>(s_cg + (size_t)K * TP);  // [K][TP] dL/dalpha_r
     float *s_cv = s_cw + (size_t)K * TP;                             // [K][TP] alpha_r T_r
@@ -149,11 +152,14 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             s_cv[(size_t)r * TP + p] = al * T;
             T = __fmaf_rn(-T, al, T);
         }
-        // mode 0: no core (K = 0); 1: every candidate is in the core; 2: compare with the last entry.
-        const int mode = K == 0 ? 0 : (n_core < K ? 1 : 2);
-        s_pc[p] = make_float4(lastz, __uint_as_float(lastg), __int_as_float(mode), 0.f);
-        if (inside && mode == 1) open_l = true;
-        if (inside && mode == 2) zmax_l = fmaxf(zmax_l, lastz);
+        // A core that is not full takes every candidate (K = 0 has no core:
+        // the record loop then skips the test altogether).
+        const bool open = n_core < K;
+        s_pc[p] = make_float2(open ? INFINITY : lastz, __uint_as_float(lastg));
+        if (inside && K > 0) {
+            if (open) open_l = true;
+            else zmax_l = fmaxf(zmax_l, lastz);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) zmax_l = fmaxf(zmax_l, __shfl_xor_sync(0xffffffffu, zmax_l, o));
     open_l = __any_sync(0xffffffffu, open_l);
@@ -208,9 +214,9 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
         const int iy0 = (int)fmaxf(ceilf(c6.z - 0.5f), (float)y0);
         const int iy1 = (int)fminf(floorf(c6.w - 0.5f), (float)y1);
         if (ix0 <= ix1 && iy0 <= iy1) {
-            const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c3 = rec[3], c4 = rec[4], c5 = rec[5];
+            const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c4 = rec[4], c5 = rec[5];
             const float zlo = rec[7].x;
-            const bool may_core = tile_open || !(zlo > tile_zmax);
+            const bool may_core = K > 0 && (tile_open || !(zlo > tile_zmax));
             float2 acc[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -218,33 +224,35 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             float wmax = 0.f;  // largest blending weight of the record in this tile
             bool touched = false;
             const int lx = lane & 7, ly = lane >> 3;
-            for (int by = iy0; by <= iy1; by += 4) {
-                const int y = by + ly;
+            // Pixel centres are integers plus 1/2, exact in FP32, so stepping
+            // them by whole pixels gives (float)x + 0.5 bit for bit.
+            const float pxl = (float)(ix0 + lx) + 0.5f;
+            for (int y = iy0 + ly; y <= iy1; y += 4) {
                 const float dy = __fsub_rn((float)y + 0.5f, c4.w);
-                const int prow = (y - y0) * TW - x0;
-                for (int bx = ix0; bx <= ix1; bx += 8) {
-                    const int x = bx + lx;
-                    if (x > ix1 || y > iy1) continue;
-                    const float dx = __fsub_rn((float)x + 0.5f, c4.z);
+                const int prow = (y - y0) * TW - x0 + ix0 + lx;
+                float pxf = pxl;
+#pragma unroll
+                for (int q = 0; q < TW / 8; ++q, pxf += 8.f) {
+                    if (ix0 + lx + 8 * q > ix1) break;
+                    const float dx = __fsub_rn(pxf, c4.z);
                     FragEval f;
                     if (!frag_alpha(quad_eval2(c0, c1, c2, dx, dy), tau_alpha, alpha_max, f)) continue;
-                    const int p = prow + x;
+                    const int p = prow + 8 * q;
                     const float al = f.alpha;
                     bool in_core = false;
                     if (may_core && al >= tau_K) {
-                        const float4 PC = s_pc[p];
-                        const int mode = __float_as_int(PC.z);
-                        if (mode == 1) {
+                        const float2 PC = s_pc[p];
+                        if (PC.x == INFINITY) {
                             in_core = true;
-                        } else if (mode == 2 && !(zlo > PC.x)) {
+                        } else if (!(zlo > PC.x)) {
                             // (depths of this splat are >= zlo, so zlo > last
                             // core depth means the fragment is not in the core)
-                            const float z = frag_depth(c3, c4, dx, dy, f.rD);
+                            const float z = frag_depth(rec[3], c4, dx, dy, f.rD);
                             in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
                         }
                     }
                     if (NOTAIL && !in_core) continue;  // an omitted tail has no gradient
-                    float dA, dc0, dc1, dc2;
+                    float dA;
                     if (in_core) {
                         const float4 PA = s_pa[p];
                         float w = 0.f, s = 0.f;
@@ -255,38 +263,40 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                                 break;
                             }
                         dA = w;
-                        dc0 = PA.x * s; dc1 = PA.y * s; dc2 = PA.z * s;
+                        gc0 = __fmaf_rn(PA.x, s, gc0);
+                        gc1 = __fmaf_rn(PA.y, s, gc1);
+                        gc2 = __fmaf_rn(PA.z, s, gc2);
                         if (VIS) wmax = fmaxf(wmax, s);
                     } else {
                         const float4 PB = s_pb[p];
                         const float k0 = s_pa[p].w;
                         const float inv = rcp_approx(1.f - al);
                         dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + k0 + PB.w * inv;
-                        dc0 = PB.x * al; dc1 = PB.y * al; dc2 = PB.z * al;
+                        gc0 = __fmaf_rn(PB.x, al, gc0);
+                        gc1 = __fmaf_rn(PB.y, al, gc1);
+                        gc2 = __fmaf_rn(PB.z, al, gc2);
                         if (VIS) wmax = fmaxf(wmax, al * s_wt[p]);
                     }
                     touched = true;
-                    gc0 += dc0; gc1 += dc1; gc2 += dc2;
-                    if (f.araw < alpha_max) {
-                        // With g = alpha dL/dalpha: dL/drho^2 = -g/2, and as
-                        // rho^2 = N / D = rho_c - 2 ln2 t, dL/dN = -e/2 and
-                        // dL/dD = e rho^2 / 2 = (rho_c e - 2 ln2 e t) / 2 for
-                        // e = g / D. The pixel adds the moments of (e, e t);
-                        // the (record, tile) sums become dL/dN and dL/dD once,
-                        // after the warp reduction.
-                        const float g = dA * al;
-                        gaa += g;
-                        const float e = g * f.rD;
-                        const float2 et = make_float2(e, e * f.t);
-                        const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
-                        const float2 ex = fmul2(et, X), ey = fmul2(et, Y);
-                        acc[0] = fadd2(acc[0], et);
-                        acc[1] = fadd2(acc[1], ex);
-                        acc[2] = fadd2(acc[2], ey);
-                        acc[3] = ffma2(ex, X, acc[3]);
-                        acc[4] = ffma2(ex, Y, acc[4]);
-                        acc[5] = ffma2(ey, Y, acc[5]);
-                    }
+                    // With g = alpha dL/dalpha: dL/drho^2 = -g/2, and as
+                    // rho^2 = N / D = rho_c - 2 ln2 t, dL/dN = -e/2 and
+                    // dL/dD = e rho^2 / 2 = (rho_c e - 2 ln2 e t) / 2 for
+                    // e = g / D. The pixel adds the moments of (e, e t); the
+                    // (record, tile) sums become dL/dN and dL/dD once, after
+                    // the warp reduction. A clamped alpha (araw >= alpha_max)
+                    // passes no gradient to the geometry: g = 0 adds nothing.
+                    const float g = f.araw < alpha_max ? dA * al : 0.f;
+                    gaa += g;
+                    const float e = g * f.rD;
+                    const float2 et = make_float2(e, e * f.t);
+                    const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
+                    const float2 ex = fmul2(et, X), ey = fmul2(et, Y);
+                    acc[0] = fadd2(acc[0], et);
+                    acc[1] = fadd2(acc[1], ex);
+                    acc[2] = fadd2(acc[2], ey);
+                    acc[3] = ffma2(ex, X, acc[3]);
+                    acc[4] = ffma2(ex, Y, acc[4]);
+                    acc[5] = ffma2(ey, Y, acc[5]);
                 }
             }
             if (VIS) {
@@ -343,6 +353,7 @@ bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     if (a.prm.K < 0 || a.prm.K > HTGS_MAX_K) return false;
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
     if (tw == 16 && th == 16) return run_bwd_mode<16, 16>(b, a, s);
+    if (tw == 32 && th == 16) return run_bwd_mode<32, 16>(b, a, s);
     if (tw == 16 && th == 8) return run_bwd_mode<16, 8>(b, a, s);
     if (tw == 8 && th == 8) return run_bwd_mode<8, 8>(b, a, s);
     return false;

@@ -370,33 +370,6 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp reduction shared by the adjoint kernels.
-// ---------------------------------------------------------------------------
-
-// Sums 16 per-lane values over the warp; afterwards lane 8q (q = 0..3) holds
-// the sums of values 4q .. 4q + 3 in v[0..3].
-__device__ __forceinline__ void warp_reduce16_to4(float (&v)[16], int lane) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool up = lane & 16;
-        const float send = up ? v[i] : v[i + 8];
-        const float keep = up ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = lane & 8;
-        const float send = up ? v[i] : v[i + 4];
-        const float keep = up ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-}
-
-// ---------------------------------------------------------------------------
 // Dispatch over tile shape and pixels per thread for one KMAX.
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT, bool NOTAIL>
@@ -414,6 +387,7 @@ template <int KMAX, int PPT, bool NOTAIL = false>
 bool dispatch_shape_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
     if (tw == 16 && th == 16) return run_fwd<KMAX, 16, 16, PPT, NOTAIL>(b, a, s);
+    if (tw == 32 && th == 16) return run_fwd<KMAX, 32, 16, (PPT <= 2 ? PPT : 2), NOTAIL>(b, a, s);
     if (tw == 16 && th == 8 && PPT <= 2) return run_fwd<KMAX, 16, 8, (PPT <= 2 ? PPT : 2), NOTAIL>(b, a, s);
     if (tw == 8 && th == 8 && PPT <= 2) return run_fwd<KMAX, 8, 8, (PPT <= 2 ? PPT : 2), NOTAIL>(b, a, s);
     return false;

@@ -13,6 +13,7 @@
 // added over the tile's warps in shared memory and reduced into global
 // memory once per (record, tile).
 #include "blend_impl.cuh"
+#include "warp_reduce.cuh"
 
 namespace htgs {
 
@@ -347,6 +348,7 @@ bool run_sorted_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
 bool launch_blend_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
     if (tw == 16 && th == 16) return run_sorted_fwd<16, 16>(b, a, s);
+    if (tw == 32 && th == 16) return run_sorted_fwd<32, 16>(b, a, s);
     if (tw == 16 && th == 8) return run_sorted_fwd<16, 8>(b, a, s);
     if (tw == 8 && th == 8) return run_sorted_fwd<8, 8>(b, a, s);
     return false;
@@ -355,6 +357,7 @@ bool launch_blend_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t
 bool launch_blend_sorted_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     const int tw = a.tiles.tile_w, th = a.tiles.tile_h;
     if (tw == 16 && th == 16) return a.vis ? run_sorted_bwd<16, 16, true>(b, a, s) : run_sorted_bwd<16, 16, false>(b, a, s);
+    if (tw == 32 && th == 16) return a.vis ? run_sorted_bwd<32, 16, true>(b, a, s) : run_sorted_bwd<32, 16, false>(b, a, s);
     if (tw == 16 && th == 8) return a.vis ? run_sorted_bwd<16, 8, true>(b, a, s) : run_sorted_bwd<16, 8, false>(b, a, s);
     if (tw == 8 && th == 8) return a.vis ? run_sorted_bwd<8, 8, true>(b, a, s) : run_sorted_bwd<8, 8, false>(b, a, s);
     return false;

@@ -34,7 +34,8 @@ def _masked_upstream(scene, cam, prm, seed):
 
 
 @pytest.mark.parametrize("degree,K,tile,ppt", [(0, 8, (16, 16), 2), (3, 4, (16, 8), 1), (3, 16, (8, 8), 2),
-                                               (1, 0, (16, 16), 4), (2, 32, (16, 16), 1)])
+                                               (1, 0, (16, 16), 4), (2, 32, (16, 16), 1), (1, 8, (32, 16), 1),
+                                               (2, 32, (32, 16), 2)])
 def test_small_scene_gradients(degree, K, tile, ppt):
     """64 Gaussians of the training-step distribution seen through a 32x32
     crop of the 1200x800 camera (principal point shifted)."""

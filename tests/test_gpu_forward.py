@@ -86,7 +86,8 @@ def test_config1_binning_matches_oracle(cfg1):
         assert ty0[gi] * th <= y0 and y1 <= (ty1[gi] + 1) * th - 1
 
 
-@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((16, 16), 4), ((16, 8), 2), ((8, 8), 1), ((8, 8), 2)])
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((16, 16), 4), ((32, 16), 1), ((32, 16), 2), ((16, 8), 2),
+                                      ((8, 8), 1), ((8, 8), 2)])
 def test_launch_shapes_agree(cfg1, tile, ppt):
     """Tile shape and pixels per thread are tuning knobs: the per-pixel
     arithmetic and the (gid-ascending) traversal order do not change."""
@@ -191,7 +192,7 @@ def test_ragged_image_and_big_splats():
     scene.log_scales += np.float32(1.0)
     cam = scenes.Camera(scenes.look_at((0.1, 0.2, -0.4), (0, 0, 3)), 75.0, 70.0, 50.3, 17.9, 0.2, 101, 37).rounded()
     prm = scenes.Params(K=4, bg=(1.0, 0.5, 0.0))
-    for tile in [(16, 16), (16, 8), (8, 8)]:
+    for tile in [(16, 16), (32, 16), (16, 8), (8, 8)]:
         img, r, g = gpu_render(scene, cam, prm, tile=tile)
         ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
         e_ok, amb_frac, _ = compare_images(img, ref, d["ambiguous"])

@@ -96,7 +96,7 @@ def test_sorted_batch_and_tile_shapes_agree():
     grads = br.backward(dls)
     want = {f: torch.zeros_like(getattr(g, f)) for f in FIELDS}
     for cam, img, dl in zip(cams, imgs, dls):
-        for tile in [(16, 16), (16, 8), (8, 8)]:
+        for tile in [(16, 16), (32, 16), (16, 8), (8, 8)]:
             r = Renderer(cam, prm, scene.n, launch=B.c_launch(tile, 1))
             ref = r.forward(g)
             assert float((img - ref).abs().max()) <= 1e-6, tile

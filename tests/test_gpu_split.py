@@ -105,7 +105,8 @@ def test_split_core_ids(dense):
     np.testing.assert_array_equal(sv["core_gid"][ok], d["core_gid"][ok])
 
 
-@pytest.mark.parametrize("K,tile,ppt", [(4, (16, 8), 2), (32, (16, 16), 1), (16, (8, 8), 2), (0, (16, 16), 4)])
+@pytest.mark.parametrize("K,tile,ppt", [(4, (16, 8), 2), (32, (16, 16), 1), (16, (8, 8), 2), (0, (16, 16), 4),
+                                         (8, (32, 16), 2)])
 def test_split_launch_shapes(K, tile, ppt):
     scene, cam = _dense(12000, seed=22, degree=0), _camera()
     prm = scenes.Params(K=K)
