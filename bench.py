@@ -392,9 +392,12 @@ def batched_leg(steps, warmup):
     return out
 
 
-def profile_case(which: str, warmup: int):
+def profile_case(which: str, warmup: int, tile=None, ppt: int = 1):
     """A few untimed steps of the headline render (fwd) or of the training
-    step (train): `warmup` steps, then 2 more, nothing else on the GPU."""
+    step (train): `warmup` steps, then 2 more, nothing else on the GPU. The
+    launch shape defaults to the one the autotuner picks for the workload on
+    a GB300 (16x16 for the render, 32x16 for the training step, 1 pixel per
+    thread)."""
     import torch
     from paper_2410_08129_gb300 import binding as B
     from paper_2410_08129_gb300 import scenes
@@ -402,7 +405,7 @@ def profile_case(which: str, warmup: int):
     if which == "fwd":
         scene, cam, prm = scenes.config2()
         g = GaussianTensors.from_scene(scene)
-        r = Renderer(cam.rounded(), prm, scene.n)
+        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (16, 16), ppt))
         img = r.image_buffer()
         r.forward(g, image=img, save=False, check=True)
         for _ in range(warmup + 2):
@@ -410,7 +413,7 @@ def profile_case(which: str, warmup: int):
     else:
         scene, target, cam, prm = scenes.config3()
         g = GaussianTensors.from_scene(scene)
-        r = Renderer(cam.rounded(), prm, scene.n)
+        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (32, 16), ppt))
         img = r.image_buffer()
         tgt = r.forward(GaussianTensors.from_scene(target), save=False, check=True).clone()
         dl = torch.empty_like(img)
@@ -438,12 +441,15 @@ def main():
     ap.add_argument("--batched-warmup", type=int, default=3)
     ap.add_argument("--profile", choices=["fwd", "train"], default=None,
                     help="run a few untimed steps of one workload (for an external profiler) and exit")
+    ap.add_argument("--profile-tile", default=None, help="tile shape WxH of --profile (default: the autotuner's pick)")
+    ap.add_argument("--profile-ppt", type=int, default=1, help="forward pixels per thread of --profile")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile:
-        profile_case(args.profile, args.warmup)
+        tile = tuple(int(v) for v in args.profile_tile.split("x")) if args.profile_tile else None
+        profile_case(args.profile, args.warmup, tile, args.profile_ppt)
         return
 
     import torch
@@ -474,6 +480,7 @@ def main():
     g = GaussianTensors.from_scene(scene)
     # Launch shape (tile, pixels per thread, staging batch) from the autotuner.
     from paper_2410_08129_gb300.autotune import autotune
+    sorted_candidates = [((16, 16), 1), ((32, 16), 1), ((16, 8), 1)]
 
     def fwd_step_for(launch_):
         rr = Renderer(cam, prm, scene.n, launch=launch_)
@@ -566,7 +573,18 @@ def main():
     # ---- the variant without per-pixel hybrid transparency (Tab. 3) -------
     sprm = scenes.Params(K=prm.K, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max,
                          bg=prm.bg, sorted_blend=True)
-    sr = Renderer(cam, sprm, scene.n, launch=B.c_launch(*fwd_shape[:2], smem_batch=fwd_shape[2]))
+    # The sorted kernels differ from the hybrid ones, so they get their own
+    # tile shape (one pixel per thread; the forward's staging batch stays 128).
+    def sorted_frame_for(launch_):
+        rr = Renderer(cam, sprm, scene.n, launch=launch_)
+        im = rr.image_buffer()
+        rr.forward(g, image=im, save=False, check=True)
+        return lambda: rr.forward(g, image=im, save=False, check=False)
+
+    best_sorted, tune_sorted = autotune(sorted_frame_for, candidates=sorted_candidates, batches=(128,),
+                                        warmup=2, repeats=5)
+    sorted_tile = (best_sorted.tile_w, best_sorted.tile_h)
+    sr = Renderer(cam, sprm, scene.n, launch=B.c_launch(sorted_tile, 1))
     simg = sr.image_buffer()
     sr.forward(g, image=simg, save=False, check=True)
     for _ in range(max(args.warmup, 3)):
@@ -676,8 +694,26 @@ def main():
     # the same training step with the variant without per-pixel HT (Tab. 3)
     stprm = scenes.Params(K=tprm.K, tau_alpha=tprm.tau_alpha, tau_K=tprm.tau_K, alpha_max=tprm.alpha_max,
                           bg=tprm.bg, sorted_blend=True)
-    str_ = Renderer(tcam, stprm, tscene.n,
-                    launch=B.c_launch(train_shape[0], train_shape[1], smem_batch=train_shape[2]))
+    def sorted_train_step_for(launch_):
+        rr = Renderer(tcam, stprm, tscene.n, launch=launch_)
+        tgt = rr.forward(tt, save=False, check=True).clone()
+        im = rr.image_buffer()
+        dl_ = torch.empty_like(im)
+        loss_ = torch.zeros(1, dtype=torch.float32, device="cuda")
+        grads_ = {k: torch.empty_like(getattr(tg, k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        rr.forward(tg, image=im, save=True, check=True)
+
+        def step():
+            rr.forward(tg, image=im, save=True, check=False)
+            B._check(B.htgs_l1_loss_grad(im, tgt, dl_, loss_), "htgs_l1_loss_grad")
+            rr.backward(tg, dl_, grads=grads_)
+        return step
+
+    best_sorted_train, tune_sorted_train = autotune(sorted_train_step_for, candidates=sorted_candidates,
+                                                    batches=(128,), warmup=1, repeats=2)
+    torch.cuda.empty_cache()
+    sorted_train_tile = (best_sorted_train.tile_w, best_sorted_train.tile_h)
+    str_ = Renderer(tcam, stprm, tscene.n, launch=B.c_launch(sorted_train_tile, 1))
     starget = str_.forward(tt, save=False, check=True).clone()
     str_.forward(tg, image=timg, save=True, check=True)
 
@@ -746,8 +782,12 @@ def main():
                     "grads_finite": gfinite},
         "filter3d": filtered,
         "no_tail": no_tail,
-        "sorted_blend": dict(sorted_blend, fwd_bwd={"value": job_throughput(1, world, sorted_train_ms),
-                                                     "unit": "steps/s", "ms_per_step": sorted_train_ms}),
+        "sorted_blend": dict(sorted_blend, tile=f"{sorted_tile[0]}x{sorted_tile[1]}",
+                             fwd_bwd={"value": job_throughput(1, world, sorted_train_ms),
+                                      "unit": "steps/s", "ms_per_step": sorted_train_ms,
+                                      "tile": f"{sorted_train_tile[0]}x{sorted_train_tile[1]}",
+                                      "autotune_ms": {f"{t[0]}x{t[1]}": round(v, 2)
+                                                      for (t, _, _), v in tune_sorted_train.items()}}),
         "batched_vs_plain": batched,
         "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,

@@ -76,7 +76,7 @@ __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KM
 // Forward (K6).
 // ---------------------------------------------------------------------------
 template <int KMAX, int TW, int TH, int PPT, bool NOTAIL>
-__global__ void __launch_bounds__(TW *TH / PPT, (PPT == 1 && KMAX <= 8) ? 1024 / (TW * TH / PPT) : 1)
+__global__ void __launch_bounds__(TW *TH / PPT, KMAX > 8 ? 1 : (PPT == 1 ? 1024 : PPT == 2 ? 512 : TW * TH / PPT) / (TW * TH / PPT))
 blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
@@ -85,8 +85,11 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int TP = TW * TH;
     extern __shared__ float4 s_dyn[];
     const int B = a.tiles.batch;
-    float4 *const s_rec = s_dyn;                                                   // [3][B][kRecF4]
-    uint32_t *const s_gid = reinterpret_cast<uint32_t *>(s_dyn + 3 * B * kRecF4);  // [3][B]
+    // Whole records in rows of 128 bytes. (Moving the cull words 6 and 7 to
+    // arrays of their own removes the bank conflicts of the per-lane cull
+    // loads but costs registers, and measured 10-15% slower.)
+    float4 *const s_rec = s_dyn;                                      // [3][B][kRecF4]
+    uint32_t *const s_gid = reinterpret_cast<uint32_t *>(s_rec + 3 * B * kRecF4);  // [3][B]
     __shared__ int s_item;
     __shared__ int s_last;
     if (a.status[kStError] != 0) return;
@@ -120,6 +123,8 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     // The warp's footprint in pixel-centre coordinates.
     const float fx0 = (float)wx0 + 0.5f, fx1 = (float)wx0 + 7.5f;
     const float fy0 = (float)wy0 + 0.5f, fy1 = (float)(wy0 + WY) - 0.5f;
+    const float fxc = (float)wx0 + 4.f, fyc = (float)wy0 + 0.5f * WY;  // its centre
+    const float fhw = 3.5f, fhh = 0.5f * WY - 0.5f;                     // and half extents
 
     const int K = a.prm.K;
     const float tau_alpha = a.prm.tau_alpha, tau_K = a.prm.tau_K, alpha_max = a.prm.alpha_max;
@@ -176,10 +181,24 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
         const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(s_rec + (size_t)(b % 3) * B * kRecF4);
         const uint32_t *gids = s_gid + (b % 3) * B;
         for (int c = 0; c < nb; c += 32) {
+            // Lane c + l tests record c + l against the warp's footprint:
+            // its box, then the axis n = A v through the cutoff ellipse
+            // p^T A p <= 1 (centred on the box), v from the ellipse's centre
+            // to the footprint's. Over the footprint n.(p - centre) >= near,
+            // over the ellipse it is <= sqrt(v^T A v): near beyond that
+            // separates them. A = 0 (no ellipse) never separates.
             bool hit = false;
             if (c + lane < nb) {
                 const float4 bb = rec[c + lane][6];
                 hit = bb.x <= fx1 && bb.y >= fx0 && bb.z <= fy1 && bb.w >= fy0;
+                if (hit) {
+                    const float4 cu = rec[c + lane][7];
+                    const float vx = fxc - 0.5f * (bb.x + bb.y), vy = fyc - 0.5f * (bb.z + bb.w);
+                    const float nx = cu.y * vx + cu.z * vy, ny = cu.z * vx + cu.w * vy;
+                    const float sv = vx * nx + vy * ny;
+                    const float near = sv - fabsf(nx) * fhw - fabsf(ny) * fhh;
+                    hit = !(near > 0.f && near * near > sv);
+                }
             }
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {

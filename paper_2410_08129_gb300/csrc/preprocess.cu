@@ -236,6 +236,46 @@ __device__ __forceinline__ void make_expansion(const Setup &S, const CamArgs &ca
 
 } // namespace
 
+// The cutoff region Q >= 0 of a record, Q = q0 + x (q1 + q3 x + q4 y) +
+// y (q2 + q5 y) about the box centre, as a matrix A = (a, b; b, c) with the
+// region inside {p : p^T A p <= 1} (p measured from the box centre): the
+// forward blend skips a warp's pixel block when an axis separates the two.
+// The ellipse is grown about its own centre to cover the offset between that
+// centre and the box centre, the rounding of the box centre (0.02 px), a
+// relative 1e-3, and the rounding of A and of the per-pixel FP32 evaluation
+// of Q, both of which scale with the condition number kappa of the quadratic
+// part (a growth of 4e-6 kappa, far above the ~4e-7 kappa they need). A region
+// that is not a bounded, well-conditioned ellipse (kappa > 1e5) gets A = 0,
+// which never separates.
+__device__ void cutoff_ellipse(const float (&q)[6], float (&A)[3]) {
+    A[0] = A[1] = A[2] = 0.f;
+    // -H = (m11, m12; m12, m22), positive definite for an ellipse.
+    const float m11 = -q[3], m12 = -0.5f * q[4], m22 = -q[5];
+    // det(-H) with the rounding of m12^2 compensated (Kahan's 2x2 determinant).
+    const float w = m12 * m12;
+    const float det = __fmaf_rn(m11, m22, -w) + __fmaf_rn(-m12, m12, w);
+    if (!(m11 > 0.f) || !(det > 0.f)) return;
+    const float half_tr = 0.5f * (m11 + m22);
+    const float disc = sqrtf(0.25f * (m11 - m22) * (m11 - m22) + m12 * m12);
+    const float mu_max = half_tr + disc, mu_min = det / mu_max;
+    const float kappa = mu_max / mu_min;
+    if (!(kappa <= 1e5f)) return;
+    // Stationary point of Q (the ellipse centre) and the maximum of Q there:
+    // -H c = -(q1, q2) / 2.
+    const float cx = 0.5f * (m22 * q[1] - m12 * q[2]) / det;
+    const float cy = 0.5f * (m11 * q[2] - m12 * q[1]) / det;
+    const float qmax = q[0] + 0.5f * (q[1] * cx + q[2] * cy);
+    if (!(qmax > 0.f)) return;
+    // Semi-axes of {p : p^T (-H / qmax) p <= 1}: sqrt(qmax / mu).
+    const float rmin = sqrtf(qmax / mu_max);
+    const float grow = 1.f + 1e-3f + 4e-6f * kappa + (sqrtf(cx * cx + cy * cy) + 0.02f) / rmin;
+    const float s = 1.f / (qmax * grow * grow);
+    if (!isfinite(s)) return;
+    A[0] = m11 * s;
+    A[1] = m12 * s;
+    A[2] = m22 * s;
+}
+
 // ---------------------------------------------------------------------------
 // K1: forward setup.
 // ---------------------------------------------------------------------------
@@ -341,7 +381,9 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
                 // ellipsoid, whose view depth spans mu_z -+ sqrt(rho_c |A_3|^2).
                 const float zext = sqrtf(rc * dot(S.A[2], S.A[2]));
                 const float zlo = (S.mu[2] - zext) - 1e-3f * zext - 1e-4f * fabsf(S.mu[2]);
-                rec[7] = make_float4(zlo, 0.f, 0.f, 0.f);
+                float cull[3];
+                cutoff_ellipse(q, cull);
+                rec[7] = make_float4(zlo, cull[0], cull[1], cull[2]);
             }
         }
         // Stage the record in the warp's shared-memory slab (float4 slots
