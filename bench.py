@@ -43,7 +43,11 @@ def _peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    """Samples nvidia-smi clocks and throttle reasons while the timed region
+    runs, every 50 ms. Entering waits for the first sample (taken right after
+    the warm-up) so that the sampler is live when the region starts; leaving
+    waits for one more, so that a region shorter than the interval is still
+    bracketed by samples."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -57,11 +61,15 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
+            return self
+        deadline = time.time() + 5.0
+        while not self.rows and time.time() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
     def _read(self):
@@ -70,6 +78,9 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         if self.proc is not None:
+            n, deadline = len(self.rows), time.time() + 0.5
+            while len(self.rows) == n and time.time() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -674,17 +685,24 @@ def main():
     torch.cuda.synchronize()
     n_train = max(5, args.steps // 5)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    s0.record(stream)
-    for _ in range(n_train):
-        train_step()
-    s1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    with ClockSampler(local) as train_clocks:
+        barrier()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(n_train):
+            train_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
     train_ms = max_over_ranks(s0.elapsed_time(s1)) / n_train
-    bwd_blend_ms = []
+    bwd_blend_ms, fwd_blend_train_ms = [], []
     for _ in range(3):
-        train_step()
+        tr.forward(tg, image=timg, save=True, check=False)
+        torch.cuda.synchronize()
+        fwd_blend_train_ms.append(bev[4].elapsed_time(bev[5]))
+        tcounters = B.htgs_get_counters(tr.workspace)
+        B._check(B.htgs_l1_loss_grad(timg, target, dl, loss), "htgs_l1_loss_grad")
+        tr.backward(tg, dl, grads=grads)
         torch.cuda.synchronize()
         bwd_blend_ms.append(bev[0].elapsed_time(bev[1]))
     st2, tinst = tr.status()
@@ -742,12 +760,55 @@ def main():
     # 1 count), 10 per core candidate (depth 6, key and compare 4) and 8K per
     # core insertion; the peak is 152 SMs x 128 FP32 lanes x 2070 MHz.
     K = prm.K
-    alg = (8 * counters["box_pairs"] + 14 * counters["kept"] + 10 * counters["admitted"]
-           + 8 * K * counters["inserted"])
+
+    def fwd_work(c, k):
+        return 8 * c["box_pairs"] + 14 * c["kept"] + 10 * c["admitted"] + 8 * k * c["inserted"]
+
+    alg = fwd_work(counters, K)
     blend_s = float(np.mean(blend_ms)) / 1e3
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6
     achieved = alg / blend_s
     traffic = recorded_traffic()
+
+    # ---- every kernel group against its own roofline ------------------------
+    # HBM-bound phases: algorithmic bytes (each byte the phase must move once)
+    # over the phase's CUDA-event time, against the measured copy bandwidth.
+    # Preprocess: parameters in (3 + 3 + 4 + 1 + 3 (deg + 1)^2 floats), the
+    # 128-byte record, the 8-byte tile rectangle and the 4-byte count out.
+    # Binning and sort: the count read and an 8-byte (key, value) write per
+    # instance (emit), a 4-byte key read (histogram), a 16-byte read and write
+    # per digit pass, a 4-byte key read (ranges).
+    # ALU-bound blends: algorithmic FP32-pipe instructions (forward as above;
+    # adjoint 8 per pixel inside a box and 28 per kept fragment: alpha 5,
+    # 1 / (1 - alpha) 2, dL/dalpha 5, colour sums 3, g, e, e t 5, the six
+    # packed moment updates and their two products 8) against the FP32 peak.
+    hbm_peak = float(peaks["hbm_gbs"]) * 1e9
+    nc = (scene.sh_degree + 1) ** 2
+    pre_bytes = scene.n * ((3 + 3 + 4 + 1 + 3 * nc) * 4 + 128 + 8 + 4)
+    n_tiles = -(-cam.width // fwd_shape[0][0]) * -(-cam.height // fwd_shape[0][1])
+    passes = -(-max(1, int(n_tiles - 1).bit_length()) // 9)
+    bin_bytes = scene.n * 4 + inst * (8 + 4 + 32 * passes + 4)
+    pre_s, bin_s = float(np.mean(pre_ms)) / 1e3, float(np.mean(bin_ms)) / 1e3
+    tfwd_s, tbwd_s = float(np.mean(fwd_blend_train_ms)) / 1e3, float(np.mean(bwd_blend_ms)) / 1e3
+    bwd_alg = 8 * tcounters["box_pairs"] + 28 * tcounters["kept"]
+
+    def line(bound, work, secs, pk, unit, scale, per_unit):
+        return {"bound": bound, "achieved": work / secs / scale, "peak": pk / scale, "unit": unit,
+                "frac": work / secs / pk, "ms": secs * 1e3, "work": work, "work_per_unit": per_unit}
+
+    kernels = {
+        "preprocess_1080p": line("hbm", pre_bytes, pre_s, hbm_peak, "GB/s", 1e9,
+                                 f"{pre_bytes // scene.n} B per Gaussian"),
+        "binning_sort_1080p": line("hbm", bin_bytes, bin_s, hbm_peak, "GB/s", 1e9,
+                                   f"4 B per Gaussian + {8 + 4 + 32 * passes + 4} B per instance ({passes} passes)"),
+        "blend_fwd_1080p": line("alu", alg, blend_s, peak, "T FP32 instr/s", 1e12,
+                                "8/box pair + 14/kept + 10/candidate + 8K/insertion"),
+        "blend_fwd_train": line("alu", fwd_work(tcounters, tprm.K), tfwd_s, peak, "T FP32 instr/s", 1e12,
+                                "8/box pair + 14/kept + 10/candidate + 8K/insertion"),
+        "blend_bwd_train": line("alu", bwd_alg, tbwd_s, peak, "T FP32 instr/s", 1e12,
+                                "8/box pair + 28/kept"),
+        "hbm_peak_source": f"hbm_gbs, {peak_src}",
+    }
 
     batched = None
     if not args.no_batched:
@@ -779,6 +840,7 @@ def main():
                                "autotune_ms": {f"{t[0]}x{t[1]}/ppt{pp}/b{bb}": round(v, 2)
                                                for (t, pp, bb), v in tune_train.items()}},
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
+                    "blend_forward_ms": float(np.mean(fwd_blend_train_ms)), "clocks": train_clocks.summary(),
                     "grads_finite": gfinite},
         "filter3d": filtered,
         "no_tail": no_tail,
@@ -793,7 +855,10 @@ def main():
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (no FP32 figure in MEASURED_PEAKS.json)"},
-        "gpu_launches": args.steps * 8,
+        "kernels": kernels,
+        # per frame: preprocess, scan, emit, histogram, the digit passes,
+        # ranges, schedule and the blend
+        "gpu_launches": args.steps * (7 + passes),
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
