@@ -83,10 +83,10 @@ def test_autograd_function_matches_direct_call():
         torch.testing.assert_close(getattr(g, f).grad, direct[f], rtol=1e-5, atol=1e-6)
 
 
-def test_training_step_distribution_crop_gradients():
-    """500k Gaussians of the training-step configuration at 1200x800 with the
-    upstream gradient on a 32x32 window: every Gaussian's gradient equals
-    the oracle's gradient of that window."""
+@pytest.fixture(scope="module")
+def training_window():
+    """500k Gaussians of the training-step configuration at 1200x800 and the
+    oracle's gradient of a 32x32 window under a random upstream gradient."""
     scene, target, cam, prm = scenes.config3()
     cam = cam.rounded()
     win = (584, 384, 32, 32)
@@ -100,7 +100,16 @@ def test_training_step_distribution_crop_gradients():
     dl = np.zeros((cam.height, cam.width, 3), np.float32)
     dl[y0:y0 + h, x0:x0 + w] = dl_win
     ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl_win, window=win)
-    got, r = _gpu_grads(scene, cam, prm, dl)
+    return scene, cam, prm, dl, ref, d
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16)])
+def test_training_step_distribution_crop_gradients(training_window, tile):
+    """Every Gaussian's gradient equals the oracle's gradient of the window,
+    at the default tile shape and at the one the autotuner picks for the
+    training step."""
+    scene, cam, prm, dl, ref, d = training_window
+    got, r = _gpu_grads(scene, cam, prm, dl, tile=tile, ppt=1)
     touched = np.abs(ref["opacity_logits"]) > 0
     assert touched.sum() > 1000
     rep = assert_grad_close(got, ref)
