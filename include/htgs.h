@@ -66,7 +66,19 @@ typedef struct {
      * scales become sqrt(s^2 + v) and the opacity is scaled by
      * prod s / sqrt(s^2 + v); v is an input, no gradient flows to it. */
     const float *filter_var;
+    /* NULL, or n records written by htgs_bake (HTGS_BAKED_FLOATS(sh_degree)
+     * floats each, 16-byte aligned): the forward then reads these instead of
+     * means .. sh and filter_var (which may be NULL). Forward only: the
+     * backward needs the raw parameters and rejects a baked scene. */
+    const float *baked;
 } htgs_gaussians;
+
+/* Floats per baked Gaussian (App. A "baking": activations folded into the
+ * parameters, every coefficient of a Gaussian in one buffer): the unit
+ * quaternion, the mean and 2 ln o, the scales (the 3D filter applied) and a
+ * pad, then the 3 (deg + 1)^2 SH coefficients; rounded up to a multiple of 4
+ * so that every record starts on a 16-byte boundary. 240 bytes at degree 3. */
+#define HTGS_BAKED_FLOATS(deg) (4 * ((12 + 3 * ((deg) + 1) * ((deg) + 1) + 3) / 4))
 
 /* Gradient outputs, same shapes as htgs_gaussians. Device pointers.
  * The last three are optional training statistics of the render (NULL to
@@ -307,6 +319,19 @@ htgs_status htgs_l1_loss_grad(const float *image, const float *target, int64_t n
 htgs_status htgs_render_static(const htgs_gaussians *gaussians, const htgs_camera *cam,
                                const htgs_params *params, const htgs_launch *launch, float *image,
                                void *stream);
+
+/* Baking (App. A): writes, for every Gaussian of `gaussians` (raw parameters,
+ * and filter_var if set), the record the forward reads when
+ * htgs_gaussians.baked points to it: q / |q|, the mean, 2 ln o and the scales
+ * after the 3D filter, and the SH coefficients, computed with the same
+ * operations as the forward's own activations, so a render of the baked scene
+ * equals a render of the raw one bit for bit.
+ *   gaussians  raw parameters (gaussians->baked must be NULL)
+ *   baked      [out] n x HTGS_BAKED_FLOATS(sh_degree) floats, device,
+ *              16-byte aligned (caller-owned)
+ * Asynchronous on `stream`. HTGS_ERR_INVALID_ARG for a NULL or misaligned
+ * buffer or invalid parameters. */
+htgs_status htgs_bake(const htgs_gaussians *gaussians, float *baked, void *stream);
 
 /* Static string for a status code. */
 const char *htgs_status_string(htgs_status status);

@@ -32,7 +32,12 @@ class Gaussians(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
                 ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
-                ("filter_var", ctypes.c_void_p)]
+                ("filter_var", ctypes.c_void_p), ("baked", ctypes.c_void_p)]
+
+
+def baked_floats(sh_degree: int) -> int:
+    """Floats per baked Gaussian (HTGS_BAKED_FLOATS)."""
+    return 4 * ((12 + 3 * (sh_degree + 1) ** 2 + 3) // 4)
 
 
 class GaussiansGrad(ctypes.Structure):
@@ -106,6 +111,8 @@ def lib():
             L.htgs_render_static.argtypes = [P(Gaussians), P(Camera), P(Params), P(Launch), ctypes.c_void_p,
                                              ctypes.c_void_p]
             L.htgs_render_static.restype = ctypes.c_int32
+            L.htgs_bake.argtypes = [P(Gaussians), ctypes.c_void_p, ctypes.c_void_p]
+            L.htgs_bake.restype = ctypes.c_int32
             L.htgs_status_string.argtypes = [ctypes.c_int32]
             L.htgs_status_string.restype = ctypes.c_char_p
             for f in ("htgs_workspace_size", "htgs_render", "htgs_render_backward", "htgs_get_error",
@@ -169,7 +176,16 @@ def c_gaussians(means, log_scales, quats, logits, sh, sh_degree, filter_var=None
         raise ValueError("filter_var needs one variance per Gaussian")
     return Gaussians(_ptr(means).value, _ptr(log_scales).value, _ptr(quats).value, _ptr(logits).value,
                      _ptr(sh).value, int(means.shape[0]), int(sh_degree),
-                     _ptr(filter_var).value if filter_var is not None else None)
+                     _ptr(filter_var).value if filter_var is not None else None, None)
+
+
+def c_baked(baked, n, sh_degree) -> Gaussians:
+    """A baked scene: n records of baked_floats(sh_degree) floats (htgs_bake)."""
+    if baked.dtype != torch.float32 or not baked.is_cuda or not baked.is_contiguous():
+        raise ValueError("baked records must be a contiguous float32 CUDA tensor")
+    if baked.numel() != n * baked_floats(sh_degree):
+        raise ValueError("baked records have the wrong size for n and sh_degree")
+    return Gaussians(None, None, None, None, None, int(n), int(sh_degree), None, _ptr(baked).value)
 
 
 def _stream(stream=None):
@@ -241,6 +257,11 @@ def htgs_l1_loss_grad(image, target, dl_dimage, loss, stream=None):
     st = lib().htgs_l1_loss_grad(_ptr(image), _ptr(target), int(image.numel()), _ptr(dl_dimage), _ptr(loss),
                                  _stream(stream))
     return int(st)
+
+
+def htgs_bake(gaussians: Gaussians, baked, stream=None):
+    """Bakes raw parameters into records (App. A); returns the status."""
+    return int(lib().htgs_bake(ctypes.byref(gaussians), _ptr(baked), _stream(stream)))
 
 
 def htgs_render_static(gaussians: Gaussians, cam, params, launch, image, stream=None):

@@ -168,8 +168,14 @@ void make_prm(const htgs_params *p, ParamArgs &a) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-htgs_status check_gaussians(const htgs_gaussians *g) {
+// A baked scene (forward only) needs its aligned records; a raw one its five
+// parameter arrays.
+htgs_status check_gaussians(const htgs_gaussians *g, bool backward = false) {
     if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return HTGS_ERR_INVALID_ARG;
+    if (g->baked) {
+        if (backward || !aligned16(g->baked)) return HTGS_ERR_INVALID_ARG;
+        return HTGS_OK;
+    }
     if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
         return HTGS_ERR_INVALID_ARG;
     if (g->n > 0 && !aligned16(g->quats)) return HTGS_ERR_INVALID_ARG;
@@ -188,10 +194,10 @@ void mark(const htgs_launch *launch, int idx, cudaStream_t s) {
     if (launch && launch->events[idx]) cudaEventRecord(static_cast<cudaEvent_t>(launch->events[idx]), s);
 }
 
-htgs_status collect(int n_views, const htgs_view *views, HostView *hv) {
+htgs_status collect(int n_views, const htgs_view *views, HostView *hv, bool backward = false) {
     if (!views || n_views < 1 || n_views > kMaxViews) return HTGS_ERR_INVALID_ARG;
     for (int v = 0; v < n_views; ++v) {
-        htgs_status st = check_gaussians(views[v].gaussians);
+        htgs_status st = check_gaussians(views[v].gaussians, backward);
         if (st) return st;
         hv[v].n = views[v].gaussians->n;
         hv[v].cam = &views[v].camera;
@@ -213,7 +219,7 @@ void make_batch(int n_views, const htgs_view *views, const Layout &L, bool backw
         make_cam(&hv.camera, d.cam);
         const htgs_gaussians *g = hv.gaussians;
         d.means = g->means; d.log_scales = g->log_scales; d.quats = g->quats;
-        d.logits = g->opacity_logits; d.sh = g->sh; d.filter_var = g->filter_var;
+        d.logits = g->opacity_logits; d.sh = g->sh; d.filter_var = g->filter_var; d.baked = g->baked;
         d.n = g->n;
         d.sh_degree = g->sh_degree;
         d.rec_off = rec;
@@ -276,7 +282,9 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
             pre.dval = at<uint32_t>(workspace, L.dvals0);
             pre.dtotal = total + 1;
         }
-        preprocess_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(b, pre);
+        bool any_baked = false;
+        for (int v = 0; v < n_views; ++v) any_baked |= views[v].gaussians->baked != nullptr;
+        launch_preprocess(any_baked, L.n_blocks, b, pre, s);
     }
     mark(launch, 1, s);
     mark(launch, 2, s);
@@ -357,7 +365,7 @@ htgs_status render_batch_backward(int n_views, const htgs_view *views, const htg
                                   const htgs_launch *launch, void *workspace, size_t workspace_bytes,
                                   int64_t capacity, void *stream) {
     HostView hv[kMaxViews];
-    htgs_status st = collect(n_views, views, hv);
+    htgs_status st = collect(n_views, views, hv, true);
     if (st) return st;
     if (!workspace || ((uintptr_t)workspace % kAlign)) return HTGS_ERR_INVALID_ARG;
     for (int v = 0; v < n_views; ++v) {
@@ -571,6 +579,19 @@ htgs_status htgs_render_batch_backward(int32_t n_views, const htgs_view *views, 
                                        int64_t instance_capacity, void *stream) {
     return render_batch_backward(n_views, views, params, launch, workspace, workspace_bytes, instance_capacity,
                                  stream);
+}
+
+htgs_status htgs_bake(const htgs_gaussians *g, float *baked, void *stream) {
+    if (!g || g->baked || !baked || !aligned16(baked)) return HTGS_ERR_INVALID_ARG;
+    htgs_status st = check_gaussians(g);
+    if (st) return st;
+    if (g->n == 0) return HTGS_OK;
+    BakeArgs a;
+    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.logits = g->opacity_logits;
+    a.sh = g->sh; a.filter_var = g->filter_var; a.baked = baked; a.n = g->n; a.sh_degree = g->sh_degree;
+    const int64_t blocks = (g->n + kPreThreads - 1) / kPreThreads;
+    bake_kernel<<<(unsigned)blocks, kPreThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
 }
 
 htgs_status htgs_get_error(void *workspace, size_t workspace_bytes, void *stream, htgs_status *status,

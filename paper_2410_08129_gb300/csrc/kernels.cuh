@@ -36,6 +36,7 @@ struct ViewDesc {
     CamArgs cam;
     const float *means, *log_scales, *quats, *logits, *sh;
     const float *filter_var;  // nullptr: no 3D filter
+    const float *baked;       // nullptr, or the baked records (then means .. filter_var are not read)
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
     float *g_vis, *g_dgrad, *g_dcount;  // optional training statistics
     float *image;          // H x W x 3
@@ -55,6 +56,7 @@ struct Batch {
     long long n_rec;
     ViewDesc v[kMaxViews];
 };
+static_assert(sizeof(Batch) <= 32764, "kernel parameter limit");
 
 // View owning record i (records are grouped by view in increasing order).
 __device__ __forceinline__ int view_of_record(const Batch &b, long long i) {
@@ -188,7 +190,16 @@ struct BlendBwdArgs {
     float *vis;            // n_rec (largest blending weight, as int bits), or nullptr
 };
 
-__global__ void preprocess_kernel(const __grid_constant__ Batch b, PreArgs a);
+// Baking of one scene (raw parameters in, HTGS_BAKED_FLOATS records out).
+struct BakeArgs {
+    const float *means, *log_scales, *quats, *logits, *sh, *filter_var;
+    float *baked;
+    long long n;
+    int sh_degree;
+};
+__global__ void bake_kernel(BakeArgs a);
+// The forward setup of every record; any_baked: some view renders baked records.
+void launch_preprocess(bool any_baked, int blocks, const Batch &b, const PreArgs &a, cudaStream_t s);
 __global__ void preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a);
 
 // Binning: scan of per-block sums, then emit (global tile, record) instances.

@@ -141,6 +141,7 @@ __device__ __forceinline__ V3 cross(V3 a, V3 b) {
 struct Setup {
     bool valid;
     float o, rho_c;    // opacity and cutoff of the rendered (filtered) Gaussian
+    float two_ln_o;    // 2 ln o of the rendered Gaussian (rho_c + 2 ln tau_alpha)
     float o_raw;       // sigmoid(logit)
     float s[3];        // scales of the rendered Gaussian
     float s_raw[3];    // exp(log-scales)
@@ -154,37 +155,10 @@ struct Setup {
     float dist;
 };
 
-__device__ __forceinline__ void setup_geometry(const float *__restrict__ means,
-                                               const float *__restrict__ log_scales,
-                                               const float *__restrict__ quats,
-                                               const float *__restrict__ logits,
-                                               const float *__restrict__ filter_var, int64_t i,
-                                               const CamArgs &cam, const ParamArgs &prm,
-                                               Setup &S) {
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-    const float l = logits[i];
-    // o = sigmoid(logit); rho_c = 2 ln(o / tau_alpha) = -2 (ln(1 + e^{-l}) + ln tau_alpha).
-    S.o = 1.f / (1.f + __expf(-l));
-    S.o_raw = S.o;
-    S.rho_c = -2.f * (log1pf(__expf(-l)) + __logf(prm.tau_alpha));
-    for (int k = 0; k < 3; ++k) S.s[k] = S.s_raw[k] = __expf(log_scales[3 * i + k]);
-    // 3D smoothing filter (Sec. 4.2): convolution with an isotropic Gaussian
-    // of variance v. Scales become sqrt(s^2 + v) and the opacity is scaled by
-    // prod s / sqrt(s^2 + v), so rho_c drops by sum ln(1 + v / s^2).
-    S.fvar = filter_var ? filter_var[i] : 0.f;
-    if (filter_var) {
-        for (int k = 0; k < 3; ++k) {
-            const float r = S.fvar / (S.s_raw[k] * S.s_raw[k]);
-            S.s[k] = S.s_raw[k] * sqrtf(1.f + r);
-            S.o *= rsqrtf(1.f + r);
-            S.rho_c -= log1pf(r);
-        }
-    }
-    const float4 qr = reinterpret_cast<const float4 *>(quats)[i];
-    S.qnorm = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
-    const float inv = 1.f / S.qnorm;
-    const float w = qr.x * inv, x = qr.y * inv, y = qr.z * inv, z = qr.w * inv;
-    S.q[0] = w; S.q[1] = x; S.q[2] = y; S.q[3] = z;
+// Rotation, view transform, cull and view direction from the activated
+// parameters in S (q, s, rho_c) and the mean.
+__device__ __forceinline__ void setup_view(float mx, float my, float mz, const CamArgs &cam, Setup &S) {
+    const float w = S.q[0], x = S.q[1], y = S.q[2], z = S.q[3];
     S.R[0][0] = 1.f - 2.f * (y * y + z * z); S.R[0][1] = 2.f * (x * y - w * z); S.R[0][2] = 2.f * (x * z + w * y);
     S.R[1][0] = 2.f * (x * y + w * z); S.R[1][1] = 1.f - 2.f * (x * x + z * z); S.R[1][2] = 2.f * (y * z - w * x);
     S.R[2][0] = 2.f * (x * z - w * y); S.R[2][1] = 2.f * (y * z + w * x); S.R[2][2] = 1.f - 2.f * (x * x + y * y);
@@ -203,6 +177,69 @@ __device__ __forceinline__ void setup_geometry(const float *__restrict__ means,
     S.dist = sqrtf(vx * vx + vy * vy + vz * vz);
     const float id = S.dist > 0.f ? 1.f / S.dist : 0.f;
     S.dir[0] = vx * id; S.dir[1] = vy * id; S.dir[2] = vz * id;
+}
+
+// The activations of Gaussian i (Sec. 3.1): unit quaternion, scales and
+// 2 ln o, with the 3D smoothing filter applied when it is given. Shared by the
+// forward setup and by baking, so both produce the same bits.
+__device__ __forceinline__ void activate(const float *__restrict__ log_scales, const float *__restrict__ quats,
+                                         const float *__restrict__ logits, const float *__restrict__ filter_var,
+                                         int64_t i, Setup &S) {
+    const float l = logits[i];
+    // o = sigmoid(logit); 2 ln o = -2 ln(1 + e^{-l}), and rho_c = 2 ln o - 2 ln tau_alpha.
+    S.o = 1.f / (1.f + __expf(-l));
+    S.o_raw = S.o;
+    float two_ln_o = -2.f * log1pf(__expf(-l));
+    for (int k = 0; k < 3; ++k) S.s[k] = S.s_raw[k] = __expf(log_scales[3 * i + k]);
+    // 3D smoothing filter (Sec. 4.2): convolution with an isotropic Gaussian
+    // of variance v. Scales become sqrt(s^2 + v) and the opacity is scaled by
+    // prod s / sqrt(s^2 + v), so 2 ln o drops by sum ln(1 + v / s^2).
+    S.fvar = filter_var ? filter_var[i] : 0.f;
+    if (filter_var) {
+        for (int k = 0; k < 3; ++k) {
+            const float r = S.fvar / (S.s_raw[k] * S.s_raw[k]);
+            S.s[k] = S.s_raw[k] * sqrtf(1.f + r);
+            S.o *= rsqrtf(1.f + r);
+            two_ln_o -= log1pf(r);
+        }
+    }
+    S.two_ln_o = two_ln_o;
+    const float4 qr = reinterpret_cast<const float4 *>(quats)[i];
+    S.qnorm = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+    const float inv = 1.f / S.qnorm;
+    S.q[0] = qr.x * inv; S.q[1] = qr.y * inv; S.q[2] = qr.z * inv; S.q[3] = qr.w * inv;
+}
+
+__device__ __forceinline__ void setup_geometry(const float *__restrict__ means,
+                                               const float *__restrict__ log_scales,
+                                               const float *__restrict__ quats,
+                                               const float *__restrict__ logits,
+                                               const float *__restrict__ filter_var, int64_t i,
+                                               const CamArgs &cam, const ParamArgs &prm,
+                                               Setup &S) {
+    // (the mean is loaded first, so that all of the Gaussian's loads are in flight together)
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    activate(log_scales, quats, logits, filter_var, i, S);
+    S.rho_c = S.two_ln_o - 2.f * __logf(prm.tau_alpha);
+    setup_view(mx, my, mz, cam, S);
+}
+
+// The same setup from a baked record (App. A): bake_kernel applied activate(),
+// so every field the forward uses is identical bit for bit. (The fields only
+// the backward uses are not available: a baked scene renders forward only.)
+__device__ __forceinline__ void setup_geometry_baked(const float *__restrict__ baked, int stride, int64_t i,
+                                                     const CamArgs &cam, const ParamArgs &prm, Setup &S) {
+    const float4 *r = reinterpret_cast<const float4 *>(baked + (size_t)i * stride);
+    const float4 q = r[0], mo = r[1], sc = r[2];
+    S.q[0] = q.x; S.q[1] = q.y; S.q[2] = q.z; S.q[3] = q.w;
+    S.two_ln_o = mo.w;
+    S.rho_c = mo.w - 2.f * __logf(prm.tau_alpha);
+    S.s[0] = sc.x; S.s[1] = sc.y; S.s[2] = sc.z;
+    S.o = S.o_raw = 0.f;
+    S.s_raw[0] = S.s_raw[1] = S.s_raw[2] = 0.f;
+    S.fvar = 0.f;
+    S.qnorm = 1.f;
+    setup_view(mo.x, mo.y, mo.z, cam, S);
 }
 
 // The expansion vectors of the Pluecker moment m and direction d about the
@@ -277,8 +314,32 @@ __device__ void cutoff_ellipse(const float (&q)[6], float (&A)[3]) {
 }
 
 // ---------------------------------------------------------------------------
+// Baking (App. A): one record per Gaussian with the activations applied, in
+// the layout setup_geometry_baked reads: [q / |q|][mean, 2 ln o][s, 0][SH..].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPreThreads) bake_kernel(BakeArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
+    if (i >= a.n) return;
+    Setup S;
+    activate(a.log_scales, a.quats, a.logits, a.filter_var, i, S);
+    const int stride = HTGS_BAKED_FLOATS(a.sh_degree);
+    float4 *r = reinterpret_cast<float4 *>(a.baked + (size_t)i * stride);
+    r[0] = make_float4(S.q[0], S.q[1], S.q[2], S.q[3]);
+    r[1] = make_float4(a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2], S.two_ln_o);
+    r[2] = make_float4(S.s[0], S.s[1], S.s[2], 0.f);
+    const int ncf = 3 * (a.sh_degree + 1) * (a.sh_degree + 1);
+    const float *sh = a.sh + (size_t)i * ncf;
+    float *dst = a.baked + (size_t)i * stride + 12;
+    for (int k = 0; k < ncf; ++k) dst[k] = sh[k];
+    for (int k = ncf; k < stride - 12; ++k) dst[k] = 0.f;
+}
+
+// ---------------------------------------------------------------------------
 // K1: forward setup.
 // ---------------------------------------------------------------------------
+// BAKED: some view of the batch renders baked records (each view is checked);
+// without it the kernel never looks for them.
+template <bool BAKED>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
     __shared__ float4 s_recs[kPreThreads / 32][32 * kRecF4];
@@ -291,7 +352,10 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
         const int64_t g = i - V.rec_off;
         const CamArgs &cam = V.cam;
         Setup S;
-        setup_geometry(V.means, V.log_scales, V.quats, V.logits, V.filter_var, g, cam, a.prm, S);
+        if (BAKED && V.baked)
+            setup_geometry_baked(V.baked, HTGS_BAKED_FLOATS(V.sh_degree), g, cam, a.prm, S);
+        else
+            setup_geometry(V.means, V.log_scales, V.quats, V.logits, V.filter_var, g, cam, a.prm, S);
         uint2 rect = make_uint2(1u, 0u);
         float4 rec[kRecF4];
         for (int k = 0; k < kRecF4; ++k) rec[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -362,7 +426,8 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
                 for (int k = 0; k < 6; ++k) q[k] = hl * (rc * d[k] - n[k]);
                 // Colour (Sec. 3.1, identical to 3DGS): max(0, 0.5 + sum Y_k sh_k).
                 const int nc = (V.sh_degree + 1) * (V.sh_degree + 1);
-                const float *sh = V.sh + g * nc * 3;
+                const float *sh = (BAKED && V.baked) ? V.baked + (size_t)g * HTGS_BAKED_FLOATS(V.sh_degree) + 12
+                                                     : V.sh + g * nc * 3;
                 float rgb[3];
                 switch (V.sh_degree) {
                 case 0: sh_colour<0>(sh, S.dir[0], S.dir[1], S.dir[2], rgb); break;
@@ -591,6 +656,13 @@ preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
         if (w > 0.f) atomicMax(reinterpret_cast<int *>(V.g_vis) + g, __float_as_int(w));
     }
     emit();
+}
+
+void launch_preprocess(bool any_baked, int blocks, const Batch &b, const PreArgs &a, cudaStream_t s) {
+    if (any_baked)
+        preprocess_kernel<true><<<blocks, kPreThreads, 0, s>>>(b, a);
+    else
+        preprocess_kernel<false><<<blocks, kPreThreads, 0, s>>>(b, a);
 }
 
 } // namespace htgs

@@ -67,6 +67,26 @@ class GaussianTensors:
     def tensors(self):
         return [getattr(self, f) for f in FIELDS]
 
+    def bake(self, stream=None) -> "BakedGaussians":
+        """The scene with its activations (and the 3D filter) folded in, every
+        coefficient of a Gaussian in one record (htgs_bake, App. A): renders
+        identically, forward only."""
+        rec = torch.empty(self.n * B.baked_floats(self.sh_degree), dtype=torch.float32, device=self.means.device)
+        B._check(B.htgs_bake(self.c_struct(), rec, stream), "htgs_bake")
+        return BakedGaussians(rec, self.n, self.sh_degree)
+
+
+@dataclasses.dataclass
+class BakedGaussians:
+    """Baked records of a scene (see GaussianTensors.bake); accepted wherever
+    a forward render takes a scene."""
+    records: torch.Tensor
+    n: int
+    sh_degree: int
+
+    def c_struct(self) -> B.Gaussians:
+        return B.c_baked(self.records, self.n, self.sh_degree)
+
 
 class Renderer:
     """Owns the caller-side buffers of one (camera, K, launch) configuration:

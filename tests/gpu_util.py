@@ -46,6 +46,31 @@ def saved_planes(r: Renderer, cam, K):
     return out
 
 
+# Near-decisions that can change the core's ids without moving the colour
+# beyond the tolerance: two core depths within the oracle's tie margin, the
+# K-th and (K+1)-th depths, alpha at tau_K. On such pixels more than one core
+# list is correct. (A fragment at the cutoff has alpha = tau_alpha < tau_K
+# and is never a core candidate.)
+CORE_NEAR = oracle.AMB_CORE_TIE | oracle.AMB_CORE_EDGE | oracle.AMB_TAUK
+
+
+def assert_core_ids(sv, d):
+    """The core (integer work) equals the oracle's, ids in depth order, on
+    every pixel without an ambiguity and without a near-decision that could
+    change it; where the only such decision is a depth tie inside the core
+    (the order of nearly equal depths), both lists hold the same ids. Returns
+    the fraction of pixels compared exactly."""
+    amb = d["ambiguous"] != 0
+    near = d["near_decision"] & CORE_NEAR
+    ok = ~amb & (near == 0)
+    np.testing.assert_array_equal(sv["n_core"][ok], d["n_core"][ok])
+    np.testing.assert_array_equal(sv["core_gid"][ok], d["core_gid"][ok])
+    tie = ~amb & (near == oracle.AMB_CORE_TIE)
+    np.testing.assert_array_equal(sv["n_core"][tie], d["n_core"][tie])
+    np.testing.assert_array_equal(np.sort(sv["core_gid"][tie], -1), np.sort(d["core_gid"][tie], -1))
+    return float(ok.mean())
+
+
 def workspace_view(r: Renderer, offset, count, dtype):
     itemsize = torch.tensor([], dtype=dtype).element_size()
     return r.workspace[offset: offset + count * itemsize].view(dtype)

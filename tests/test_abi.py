@@ -87,3 +87,18 @@ def test_oracle_is_not_linked_into_the_library(lib_path):
     assert "og_" not in out
     deps = subprocess.run(["readelf", "-d", lib_path], capture_output=True, text=True, check=True).stdout
     assert "htgs_oracle" not in deps
+
+
+def test_baked_record_size_matches_the_header():
+    """HTGS_BAKED_FLOATS(deg) of include/htgs.h, evaluated as written, equals
+    the binding's baked_floats: 12 floats of activated geometry, 3 (deg + 1)^2
+    SH coefficients, rounded up to a multiple of 4."""
+    from paper_2410_08129_gb300 import binding as B
+    hdr = open(os.path.join(ROOT, "include", "htgs.h")).read()
+    m = re.search(r"#define HTGS_BAKED_FLOATS\(deg\)\s+(.+)", hdr)
+    assert m
+    expr = m.group(1).strip().replace("/", "//")
+    for deg in range(4):
+        assert eval(expr, {"deg": deg}) == B.baked_floats(deg)
+        assert B.baked_floats(deg) % 4 == 0 and B.baked_floats(deg) >= 12 + 3 * (deg + 1) ** 2
+    assert B.baked_floats(3) * 4 == 240
