@@ -592,6 +592,28 @@ def main():
                          "Gaussian); image identical to the raw render"}
     del kr, kg, kimg
 
+    # ---- the headline frame at K = 4 and K = 16 (the K sweep) ----------------
+    k_sweep = {}
+    for kk in (4, 16):
+        kprm = scenes.Params(K=kk, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max, bg=prm.bg)
+        ksr = Renderer(cam, kprm, scene.n, launch=B.c_launch(*fwd_shape[:2], smem_batch=fwd_shape[2]))
+        ksimg = ksr.image_buffer()
+        ksr.forward(g, image=ksimg, save=False, check=True)
+        for _ in range(max(args.warmup, 3)):
+            ksr.forward(g, image=ksimg, save=False, check=False)
+        torch.cuda.synchronize()
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        for _ in range(args.steps):
+            ksr.forward(g, image=ksimg, save=False, check=False)
+        w1.record(stream)
+        torch.cuda.synchronize()
+        assert ksr.status()[0] == B.HTGS_OK
+        kms = max_over_ranks(w0.elapsed_time(w1))
+        k_sweep[str(kk)] = {"value": job_throughput(args.steps, world, kms), "unit": UNIT,
+                            "ms_per_step": kms / args.steps}
+        del ksr, ksimg
+
     # ---- the same frame rendered without the tail (inference variant) ------
     nprm = scenes.Params(K=prm.K, tau_alpha=prm.tau_alpha, tau_K=prm.tau_K, alpha_max=prm.alpha_max,
                          bg=prm.bg, no_tail=True)
@@ -872,9 +894,42 @@ def main():
         "hbm_peak_source": f"hbm_gbs, {peak_src}",
     }
 
+    # ---- stress: 6M Gaussians with flat, near-plane and opaque splats --------
+    # (5% with one scale 1e-7, 1% near the camera or the near plane, 1% at
+    # o = 0.999), 1920x1080, forward + backward at K = 4, 8, 16, 32.
+    del tr, tg, tt, grads, timg, dl, target
+    torch.cuda.empty_cache()
+    sscene, scam, _ = scenes.config5()
+    scam = scam.rounded()
+    sgs = GaussianTensors.from_scene(sscene)
+    stress = {}
+    for kk in (4, 8, 16, 32):
+        srr = Renderer(scam, scenes.Params(K=kk), sscene.n,
+                       launch=B.c_launch(*fwd_shape[:2], smem_batch=fwd_shape[2]))
+        simg = srr.forward(sgs, save=True, check=True)
+        sdl = torch.randn(simg.shape, device=simg.device, generator=torch.Generator(device=simg.device).manual_seed(5))
+        sgrads = srr.backward(sgs, sdl)
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(3):
+            srr.forward(sgs, image=simg, save=True, check=False)
+            srr.backward(sgs, sdl, grads=sgrads)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        st_s, sinst = srr.status()
+        assert st_s == B.HTGS_OK
+        finite = bool(torch.isfinite(simg).all()) and all(bool(torch.isfinite(v).all()) for v in sgrads.values())
+        sms = max_over_ranks(x0.elapsed_time(x1)) / 3
+        stress[str(kk)] = {"value": job_throughput(1, world, sms), "unit": "steps/s", "ms_per_step": sms,
+                           "instances": sinst, "finite": finite}
+        del srr, simg, sdl, sgrads
+    del sgs, sscene
+    torch.cuda.empty_cache()
+
     batched = None
     if not args.no_batched:
-        del r, tr, g, tg, tt, grads, image, timg, dl, target
+        del r, g, image
         torch.cuda.empty_cache()
         barrier()
         batched = batched_leg(args.batched_steps, args.batched_warmup)
@@ -904,6 +959,9 @@ def main():
                     "instances": tinst, "blend_backward_ms": float(np.mean(bwd_blend_ms)),
                     "blend_forward_ms": float(np.mean(fwd_blend_train_ms)), "clocks": train_clocks.summary(),
                     "grads_finite": gfinite},
+        "k_sweep": k_sweep,
+        "stress": dict(stress, workload="6M clustered Gaussians at 1920x1080: 5% flat (one scale 1e-7), 1% at "
+                                        "the camera or the near plane, 1% at o = 0.999; render + backward"),
         "filter3d": filtered,
         "baked": baked,
         "no_tail": no_tail,
