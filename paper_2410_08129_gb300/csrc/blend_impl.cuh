@@ -75,8 +75,19 @@ __device__ __forceinline__ void core_insert(float (&cz)[KMAX], uint32_t (&cg)[KM
 // ---------------------------------------------------------------------------
 // Forward (K6).
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM the register budget is sized for: at one pixel per
+// thread 4 (K <= 8), 3 (K = 16) or 2 (K = 32) CTAs of 256 threads, where the
+// core's 2K registers still fit without spilling; 2 x 128 threads at two
+// pixels per thread (K <= 8).
+template <int KMAX, int PPT, int NT>
+constexpr int fwd_min_blocks() {
+    constexpr int threads = PPT == 1 ? (KMAX <= 8 ? 1024 : KMAX <= 16 ? 768 : 512)
+                                     : (PPT == 2 && KMAX <= 8 ? 512 : NT);
+    return threads / NT > 0 ? threads / NT : 1;
+}
+
 template <int KMAX, int TW, int TH, int PPT, bool NOTAIL>
-__global__ void __launch_bounds__(TW *TH / PPT, KMAX > 8 ? 1 : (PPT == 1 ? 1024 : PPT == 2 ? 512 : TW * TH / PPT) / (TW * TH / PPT))
+__global__ void __launch_bounds__(TW *TH / PPT, fwd_min_blocks<KMAX, PPT, TW * TH / PPT>())
 blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int NT = TW * TH / PPT;
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
