@@ -153,7 +153,7 @@ __host__ __device__ inline size_t sorted_bwd_smem_bytes() {
 }
 
 template <int TW, int TH, bool VIS>
-__global__ void __launch_bounds__(TW *TH, 512 / (TW * TH) > 0 ? 512 / (TW * TH) : 1)
+__global__ void __launch_bounds__(TW *TH, 768 / (TW * TH) > 0 ? 768 / (TW * TH) : 1)
 blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
     constexpr int NT = TW * TH;
     constexpr int WPR = TW / 8;
