@@ -102,22 +102,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def source_digest(names) -> str:
+    """sha256 of the kernel sources with comments and blank lines removed, so
+    that a comment edit does not retire counters taken on unchanged code."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2410_08129_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
+    return h.hexdigest()
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the forward blend on the headline workload,
     as measured by ncu (profiles/blend_fwd_traffic.json); None when the
-    kernel's sources changed since the counters were taken."""
-    import hashlib
+    kernel's code changed since the counters were taken."""
     prof = os.path.join(ROOT, "profiles", "blend_fwd_traffic.json")
     try:
         with open(prof) as f:
             rec = json.load(f)
-        h = hashlib.sha256()
-        for name in rec["sources"]:
-            with open(os.path.join(ROOT, "paper_2410_08129_gb300", "csrc", name), "rb") as f:
-                h.update(f.read())
+        digest = source_digest(rec["sources"])
     except (OSError, ValueError, KeyError):
         return None
-    return rec.get("bytes_per_launch_1080p_1M") if h.hexdigest() == rec.get("sources_sha256") else None
+    return rec.get("bytes_per_launch_1080p_1M") if digest == rec.get("sources_code_sha256") else None
 
 
 def reduce_max(x: float, world: int, device) -> float:

@@ -7,9 +7,10 @@
 // instance list (gid ascending, no depth order) is staged through shared
 // memory in batches of records, three buffers deep with cp.async so that the
 // gathers of the next two batches overlap the evaluation of the current one.
-// A warp first culls a batch against its footprint (one bounding-box test per
-// lane and record, one ballot per 32 records) and evaluates only the records
-// that touch it. For each pixel one packed FP32x2 evaluation gives the pair
+// A warp first culls a batch against its footprint (per lane and record a
+// bounding-box test and one separating axis against the record's cutoff
+// ellipse; one ballot per 32 records) and evaluates only the records that
+// touch it. For each pixel one packed FP32x2 evaluation gives the pair
 // (Q, D) of a record: Q >= 0 decides rho^2 <= rho_c and D gives alpha. Kept
 // fragments update the per-pixel order-independent sums over all fragments
 // (sum alpha, sum alpha c, prod (1 - alpha), count) and, when
