@@ -144,6 +144,11 @@ typedef struct {
     int32_t smem_batch;       /* records the forward blend stages per shared-memory batch:
                                  32, 64 or 128 (default, also for 0) */
     void *events[6];
+    int32_t test_lookback_stall; /* test of the failure path, 0 otherwise: in the tile sort's first
+                                    digit pass the first block also waits for a look-back word that
+                                    nothing writes; the bounded wait gives up, the sort completes
+                                    correctly, the blend is skipped and htgs_get_error reports
+                                    HTGS_ERR_TIMEOUT */
 } htgs_launch;
 
 /* Sizes of the caller-owned buffers for one camera.

@@ -62,7 +62,8 @@ class Params(ctypes.Structure):
 class Launch(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("px_per_thread", ctypes.c_int32), ("depth_bits", ctypes.c_int32),
-                ("smem_batch", ctypes.c_int32), ("events", ctypes.c_void_p * 6)]
+                ("smem_batch", ctypes.c_int32), ("events", ctypes.c_void_p * 6),
+                ("test_lookback_stall", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -155,10 +156,12 @@ def c_params(p) -> Params:
     return q
 
 
-def c_launch(tile=(16, 16), px_per_thread=0, depth_bits=0, events=None, smem_batch=0) -> Launch:
+def c_launch(tile=(16, 16), px_per_thread=0, depth_bits=0, events=None, smem_batch=0,
+             test_lookback_stall=0) -> Launch:
     """events: up to 6 torch.cuda.Event(enable_timing=True) (or None) recorded
     around the render phases, see htgs_launch in include/htgs.h."""
     L = Launch(int(tile[0]), int(tile[1]), int(px_per_thread), int(depth_bits), int(smem_batch))
+    L.test_lookback_stall = int(test_lookback_stall)
     for i, e in enumerate(events or []):
         L.events[i] = e.cuda_event if e is not None else None
     return L

@@ -105,8 +105,9 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     L.ghist = o; o = align_up(o + kMaxPasses * kMaxRadix * sizeof(uint32_t));
     L.tickets = o; o = align_up(o + kMaxPasses * sizeof(uint32_t));
     L.ranges = o; o = align_up(o + (size_t)n_tiles * sizeof(uint2));
-    L.lookback = o;
-    o = align_up(o + (size_t)L.passes * L.n_sort_blocks * ((size_t)1 << L.digit_bits) * sizeof(unsigned long long));
+    L.lookback = o;  // (plus one word nothing writes: the target of htgs_launch.test_lookback_stall)
+    o = align_up(o + ((size_t)L.passes * L.n_sort_blocks * ((size_t)1 << L.digit_bits) + 1) *
+                         sizeof(unsigned long long));
     // Split-tile slots: enough for chunks of kMinChunk over the whole capacity, at most kMaxSlots.
     L.slots_cap = (int)std::min<int64_t>(kMaxSlots, 2 * ((capacity + kMinChunk - 1) / kMinChunk) + 2);
     L.max_items = (int)(n_tiles + L.slots_cap);
@@ -327,6 +328,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     so.lookback = at<unsigned long long>(workspace, L.lookback);
     so.tickets = at<uint32_t>(workspace, L.tickets);
     so.n_sort_blocks = L.n_sort_blocks; so.status = status;
+    so.stall_first = (launch && launch->test_lookback_stall) ? 1 : 0;
     const int sb = launch_sort(so, s);
 
     RangeArgs ra{};
@@ -340,6 +342,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     sc.slots_cap = L.slots_cap;
     sc.items = at<int4>(workspace, L.items);
     sc.n_items = at<uint32_t>(workspace, L.n_items);
+    sc.status = status;
     launch_schedule(sc, s);
 
     BlendFwdArgs ba{};

@@ -288,6 +288,21 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
         unsigned long long *lb = a.lookback + ((size_t)pass * a.n_sort_blocks) * R;
         unsigned long long excl = 0;
         if (t == 0) {
+            if (pass == 0 && a.stall_first) {
+                // Test of the bounded wait: the word after the look-back
+                // array is zeroed with it and never written. The limit is an
+                // eighth of the others', so the blocks waiting on this one
+                // still see its counts and the sort completes correctly.
+                const unsigned long long *never = a.lookback + (size_t)a.passes * a.n_sort_blocks * R;
+                uint32_t spins = 0;
+                while ((ld_relaxed(never) & ~kCountMask) == 0) {
+                    if (++spins > kSpinLimit / 8) {
+                        set_error(a.status, HTGS_ERR_TIMEOUT);
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(64);
+                }
+            }
             st_relaxed(&lb[d], kFlagInc | run);
         } else {
             st_relaxed(&lb[(size_t)t * R + d], kFlagAgg | run);
@@ -375,6 +390,12 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a)
     __shared__ uint32_t s_pos[kSchedBuckets];
     __shared__ uint32_t s_slots;
     const int tid = threadIdx.x;
+    // After a recorded failure the tile ranges may not describe the list
+    // (keys a bounded wait left unsorted): schedule nothing.
+    if (a.status[kStError] != 0) {
+        if (tid == 0) *a.n_items = 0;
+        return;
+    }
     const uint64_t total = *a.total;
     uint64_t chunk = (total + kChunkDiv - 1) / kChunkDiv;
     if (chunk < kMinChunk) chunk = kMinChunk;

@@ -124,6 +124,7 @@ struct SortArgs {
     uint32_t *tickets;     // kMaxPasses
     int n_sort_blocks;
     int *status;
+    int stall_first;       // 1 only to test the bounded wait: pass 0's first block waits on a word nothing writes
 };
 
 struct RangeArgs {
@@ -142,6 +143,7 @@ struct ScheduleArgs {
     int slots_cap;         // partial-state slots available
     int4 *items;           // n_tiles + slots_cap
     uint32_t *n_items;
+    const int *status;     // a recorded failure (overflow, a wait that gave up): no items
 };
 
 // A work item names an existing tile and a chunk k < m whose slots fit.
