@@ -43,24 +43,30 @@ def _time(step_for_launch, launch, warmup, repeats):
     return e0.elapsed_time(e1) / repeats
 
 
-def autotune(step_for_launch, key=None, candidates=CANDIDATES, batches=BATCHES, warmup=1, repeats=3):
+def autotune(step_for_launch, key=None, candidates=CANDIDATES, batches=BATCHES, warmup=1, repeats=3,
+             timer=_time):
     """step_for_launch(launch) -> callable running one step on the current
     stream with that launch configuration (the callable may allocate on its
-    first use). Returns (best htgs_launch, {(tile, ppt, batch): ms})."""
+    first use). Returns (best htgs_launch, {(tile, ppt, batch): ms}). A
+    candidate whose step raises HTGSError (a shape the library does not
+    support for this configuration) is skipped; timer(step_for_launch,
+    launch, warmup, repeats) -> ms measures one candidate."""
     if key is not None and key in _cache:
         tile, ppt, batch = _cache[key][0]
         return B.c_launch(tile, ppt, smem_batch=batch), _cache[key][1]
     times = {}
     for tile, ppt in candidates:
         try:
-            times[(tile, ppt, batches[0])] = _time(step_for_launch, B.c_launch(tile, ppt, smem_batch=batches[0]),
+            times[(tile, ppt, batches[0])] = timer(step_for_launch, B.c_launch(tile, ppt, smem_batch=batches[0]),
                                                    warmup, repeats)
         except B.HTGSError:
             continue
+    if not times:
+        raise B.HTGSError(B.HTGS_ERR_NOT_SUPPORTED, "autotune: no candidate launch ran")
     tile, ppt, _ = min(times, key=times.get)
     for batch in batches[1:]:
         try:
-            times[(tile, ppt, batch)] = _time(step_for_launch, B.c_launch(tile, ppt, smem_batch=batch),
+            times[(tile, ppt, batch)] = timer(step_for_launch, B.c_launch(tile, ppt, smem_batch=batch),
                                               warmup, repeats)
         except B.HTGSError:
             continue
