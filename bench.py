@@ -978,6 +978,7 @@ def main():
         "baked": baked,
         "no_tail": no_tail,
         "sorted_blend": dict(sorted_blend, tile=f"{sorted_tile[0]}x{sorted_tile[1]}",
+                             autotune_ms={f"{t[0]}x{t[1]}": round(v, 4) for (t, _, _), v in tune_sorted.items()},
                              fwd_bwd={"value": job_throughput(1, world, sorted_train_ms),
                                       "unit": "steps/s", "ms_per_step": sorted_train_ms,
                                       "tile": f"{sorted_train_tile[0]}x{sorted_train_tile[1]}",
