@@ -19,6 +19,15 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   render_backward -- pinned (FP64 central finite differences of render)
   sh_basis      -- pinned (quadrature orthonormality, complex-SH identities)
   bin           -- pinned (brute-force tile/rectangle overlap)
+  3D filter     -- pinned (density against a quadrature of the convolution
+                   integral, rho^2 and alpha from the summed covariance, zero
+                   variance is no filter, gradient by central differences)
+  no-tail and mean-depth-sorted blending -- pinned (the core's sorted blend
+                   over the background; an independent per-pixel blend in
+                   mean-depth order with early termination, equal to the
+                   hybrid blend when the orders agree; central differences)
+  training statistics -- pinned (largest blending weight against a per-pixel
+                   recomputation; half distance times the mean gradient norm)
 """
 from __future__ import annotations
 
