@@ -128,9 +128,9 @@ typedef struct {
                          the transmittance below 1e-4; K, tau_K and no_tail are ignored */
 } htgs_params;
 
-/* Tuning knobs (none changes the result beyond float rounding order) and
- * optional timing hooks. A NULL htgs_launch* or a zero field selects the
- * default.
+/* Tuning knobs (none changes the result beyond float rounding order),
+ * optional timing hooks and a test hook of the failure path. A NULL
+ * htgs_launch* or a zero field selects the default.
  *   events  host array of 6 cudaEvent_t handles (created by the caller; any
  *           entry may be NULL). htgs_render records [0]/[1] around the
  *           preprocess, [2]/[3] around binning and sorting and [4]/[5]
@@ -138,8 +138,10 @@ typedef struct {
  *           the blend adjoint and [2]/[3] around the preprocess adjoint. */
 typedef struct {
     int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 32x16, 16x8 or 8x8 */
-    int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4
-                                 (1 when params.no_tail is set) */
+    int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4, a
+                                 request the kernels may narrow: 1 when params.no_tail is set or
+                                 K > 16, at most 2 when K > 8; 4 needs 16x16 tiles (32x16 runs it
+                                 as 2, 16x8 and 8x8 return HTGS_ERR_NOT_SUPPORTED) */
     int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */
     int32_t smem_batch;       /* records the forward blend stages per shared-memory batch:
                                  32, 64 or 128 (default, also for 0) */
