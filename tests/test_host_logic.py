@@ -1,5 +1,9 @@
 """Host-side helpers of the Python layer (no GPU): the instance-capacity
 growth after an overflow, the baked-record size and the launch structure."""
+import os
+import subprocess
+import sys
+
 import pytest
 
 from paper_2410_08129_gb300 import binding as B
@@ -29,3 +33,14 @@ def test_launch_struct_fields():
         (32, 16, 2, 0, 64, 1)
     assert B.c_launch().test_lookback_stall == 0
     assert all(e is None for e in B.c_launch().events)
+
+
+def test_the_package_never_imports_the_oracle():
+    """The product path (the package and its binding) has no route to the
+    CPU oracle: importing every module leaves the oracle unloaded."""
+    code = ("import sys, paper_2410_08129_gb300.binding, paper_2410_08129_gb300.renderer, "
+            "paper_2410_08129_gb300.autotune, paper_2410_08129_gb300.scenes, paper_2410_08129_gb300.build; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, check=True)
+    assert out.stdout.strip() == "False"
