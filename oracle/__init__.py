@@ -107,7 +107,8 @@ class _Diag(ctypes.Structure):
                 ("core_gid", ctypes.c_void_p), ("T_core", ctypes.c_void_p),
                 ("T_tail", ctypes.c_void_p), ("A_tail", ctypes.c_void_p),
                 ("c_tail", ctypes.c_void_p), ("ambiguous", ctypes.c_void_p),
-                ("frag_hash", ctypes.c_void_p), ("near_decision", ctypes.c_void_p)]
+                ("frag_hash", ctypes.c_void_p), ("near_decision", ctypes.c_void_p),
+                ("amb_effect", ctypes.c_void_p)]
 
 
 def _load():
@@ -120,6 +121,9 @@ def _load():
             lib.og_preprocess.argtypes = [P(_Gaussians), P(_Camera), P(_Params), ctypes.c_void_p]
             lib.og_render.argtypes = [P(_Gaussians), P(_Camera), P(_Params), P(_Window),
                                       ctypes.c_void_p, P(_Diag)]
+            lib.og_render_boxed.argtypes = [P(_Gaussians), P(_Camera), P(_Params), P(_Window),
+                                            ctypes.c_int32, ctypes.c_void_p, P(_Diag),
+                                            P(ctypes.c_int64)]
             lib.og_render_splats.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(_Camera), P(_Params),
                                              P(_Window), ctypes.c_void_p, P(_Diag)]
             lib.og_render_backward.argtypes = [P(_Gaussians), P(_Camera), P(_Params), P(_Window),
@@ -230,9 +234,24 @@ def eval_pair(splats: np.ndarray, gid: int, xs: float, ys: float):
     return bool(hit), out[0], out[1], out[2], out[3], out[4]
 
 
-def render(scene, cam, params, window=None, diagnostics: bool = False):
+def render(scene, cam, params, window=None, diagnostics: bool = False, box_margin=None):
     """Brute-force FP64 render of a pixel window; returns the (h, w, 3) image,
-    plus a dict of per-pixel diagnostics when requested."""
+    plus a dict of per-pixel diagnostics when requested.
+
+    With ``box_margin`` (pixels) only the Gaussians whose FP64 covered-pixel
+    rectangle (Sec. 3.2's tight box), grown by that margin, meets the window
+    are tested against its pixels; every other pair lies outside the box and
+    is rejected by the brute force as well, so the result is the same (the
+    tests check this). The diagnostics then also hold ``n_tested``, the
+    number of Gaussians tested.
+
+    Diagnostics per pixel: fragment count, core size and ids (depth order),
+    T_core, T_tail, A_tail, c_tail, ``near_decision`` (bits of every decision
+    within rounding of its threshold), ``ambiguous`` (those whose flip alone
+    moves the colour by more than 2e-5) and ``amb_effect`` (the sum over the
+    near-decisions of the largest channel move that flipping each one alone
+    makes: a per-pixel bound, to first order, on how far a result that takes
+    any of them the other way can lie from this one)."""
     lib = _load()
     keep = _Keep(scene)
     c, p = _camera(cam), _params(params)
@@ -246,12 +265,20 @@ def render(scene, cam, params, window=None, diagnostics: bool = False):
                  core_gid=np.zeros((h, w, K), np.int32), T_core=np.zeros((h, w)),
                  T_tail=np.zeros((h, w)), A_tail=np.zeros((h, w)), c_tail=np.zeros((h, w, 3)),
                  ambiguous=np.zeros((h, w), np.int32), frag_hash=np.zeros((h, w), np.uint64),
-                 near_decision=np.zeros((h, w), np.int32))
+                 near_decision=np.zeros((h, w), np.int32), amb_effect=np.zeros((h, w)))
         diag = _Diag(*[d[k].ctypes.data for k in ("n_frag", "n_core", "core_gid", "T_core",
                                                    "T_tail", "A_tail", "c_tail", "ambiguous",
-                                                   "frag_hash", "near_decision")])
-    rc = lib.og_render(ctypes.byref(keep.g), ctypes.byref(c), ctypes.byref(p), ctypes.byref(win),
-                       img.ctypes.data, ctypes.byref(diag) if diag is not None else None)
+                                                   "frag_hash", "near_decision", "amb_effect")])
+    dptr = ctypes.byref(diag) if diag is not None else None
+    if box_margin is None:
+        rc = lib.og_render(ctypes.byref(keep.g), ctypes.byref(c), ctypes.byref(p), ctypes.byref(win),
+                           img.ctypes.data, dptr)
+    else:
+        tested = ctypes.c_int64(0)
+        rc = lib.og_render_boxed(ctypes.byref(keep.g), ctypes.byref(c), ctypes.byref(p),
+                                 ctypes.byref(win), int(box_margin), img.ctypes.data, dptr,
+                                 ctypes.byref(tested))
+        d["n_tested"] = int(tested.value)
     if rc:
         raise RuntimeError(f"og_render failed ({rc})")
     if diagnostics:

@@ -105,6 +105,8 @@ typedef struct {
     int32_t *ambiguous;    /* w*h: near-decisions whose flip moves the colour by > 2e-5 */
     uint64_t *frag_hash;   /* w*h: order-independent hash of the fragment gid set */
     int32_t *near_decision;/* w*h: every near-decision, whatever its effect on the colour */
+    double *amb_effect;    /* w*h: sum over the pixel's near-decisions of the largest channel
+                              change that flipping that one decision alone makes to the colour */
 } og_pixel_diag;
 
 /* Near-decision flags. A discrete decision that single precision may take
@@ -487,7 +489,8 @@ typedef struct {
     double z, alpha, a_raw, rho2;
     double c[3];
     int64_t gid;
-    int32_t force; /* 0: core admission by alpha >= tau_K; +1 / -1: forced in / out */
+    int32_t force; /* hybrid: 0 core admission by alpha >= tau_K, +1 / -1 forced in / out;
+                      sorted blending: +1 never stop at this fragment, -1 stop before it */
     double zmean;  /* view-space depth of the Gaussian's mean (sorted blending) */
 } og_frag;
 
@@ -588,9 +591,11 @@ static void og_blend_sorted(og_fragvec *F, const og_params *prm, og_pixel_result
     for (int64_t i = 0; i < F->n; ++i) {
         const og_frag *f = &F->f[i];
         const double Tn = T * (1.0 - f->alpha);
-        if (fabs(Tn - OG_SORTED_TMIN) <= 1e-6 * OG_SORTED_TMIN + 1e-7 * T) res->amb |= OG_AMB_TERM;
-        if (Tn < OG_SORTED_TMIN) break;
+        /* The order of the last blended fragment and the first one left out
+           also decides the result, so that pair is checked before the stop. */
         if (i > 0 && fabs(f->zmean - F->f[i - 1].zmean) <= OG_DEPTH_REL * fabs(f->zmean)) res->amb |= OG_AMB_ORDER;
+        if (fabs(Tn - OG_SORTED_TMIN) <= 1e-6 * OG_SORTED_TMIN + 1e-7 * T) res->amb |= OG_AMB_TERM;
+        if (f->force < 0 || (Tn < OG_SORTED_TMIN && f->force <= 0)) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += f->alpha * T * f->c[ch];
         T = Tn;
         ++used;
@@ -668,6 +673,10 @@ typedef struct {
     double *image;
     og_pixel_diag *diag;
     int err;
+    const int64_t *idx;   /* NULL: every Gaussian; else the n_idx Gaussians to test */
+    int64_t n_idx;
+    const int64_t *grown; /* with idx: per tested Gaussian its grown pixel rectangle
+                             (x0, x1, y0, y1); pixels outside it are not tested */
 } og_render_ctx;
 
 /* Blends a copy of src[0..n) (og_blend reorders its input). */
@@ -679,21 +688,29 @@ static void og_blend_copy(const og_frag *src, int64_t n, og_fragvec *scratch, co
     og_blend(scratch, prm, res);
 }
 
-static int og_moves(const og_pixel_result *a, const og_pixel_result *b) {
-    for (int ch = 0; ch < 3; ++ch)
-        if (fabs(a->C[ch] - b->C[ch]) > OG_EFFECT_TOL) return 1;
-    return 0;
+/* Largest channel change between two blends of the same pixel. */
+static double og_move(const og_pixel_result *a, const og_pixel_result *b) {
+    double m = 0;
+    for (int ch = 0; ch < 3; ++ch) {
+        const double e = fabs(a->C[ch] - b->C[ch]);
+        if (e > m) m = e;
+    }
+    return m;
 }
 
-/* Re-blends with each near-decision flipped; returns the bits whose flip
-   moves the colour by more than OG_EFFECT_TOL. */
+/* Re-blends with each near-decision flipped, one at a time; returns the bits
+   whose flip moves the colour by more than OG_EFFECT_TOL and adds every
+   flip's move to *budget. */
 static int32_t og_effects(const og_fragvec *F0, const og_fragvec *Bd, const og_fragvec *Fs,
                           const og_pixel_result *res, const og_params *prm, og_fragvec *work,
-                          og_fragvec *scratch) {
+                          og_fragvec *scratch, double *budget) {
+    /* (Sorted blending has no core: only its cutoff flips are evaluated here.) */
+    const int hybrid = !prm->sorted_blend;
     int32_t amb = 0;
+    double sum = 0, mv;
     og_pixel_result alt;
     /* Cutoff: drop a kept borderline fragment, or add a rejected one. */
-    for (int64_t b = 0; b < Bd->n && !(amb & OG_AMB_CUTOFF); ++b) {
+    for (int64_t b = 0; b < Bd->n; ++b) {
         const og_frag *x = &Bd->f[b];
         work->n = 0;
         int present = 0;
@@ -703,25 +720,26 @@ static int32_t og_effects(const og_fragvec *F0, const og_fragvec *Bd, const og_f
         }
         if (!present) og_push(work, x);
         og_blend_copy(work->f, work->n, scratch, prm, &alt);
-        if (og_moves(&alt, res)) amb |= OG_AMB_CUTOFF;
+        sum += (mv = og_move(&alt, res));
+        if (mv > OG_EFFECT_TOL) amb |= OG_AMB_CUTOFF;
     }
     /* Core admission: force the opposite side of tau_K. */
-    for (int64_t i = 0; i < F0->n && !(amb & OG_AMB_TAUK); ++i) {
+    for (int64_t i = 0; i < F0->n && hybrid; ++i) {
         if (fabs(F0->f[i].alpha - prm->tau_K) > OG_TAUK_ABS) continue;
         work->n = 0;
         for (int64_t k = 0; k < F0->n; ++k) og_push(work, &F0->f[k]);
         work->f[i].force = F0->f[i].alpha >= prm->tau_K ? -1 : 1;
         og_blend_copy(work->f, work->n, scratch, prm, &alt);
-        if (og_moves(&alt, res)) amb |= OG_AMB_TAUK;
+        sum += (mv = og_move(&alt, res));
+        if (mv > OG_EFFECT_TOL) amb |= OG_AMB_TAUK;
     }
     /* Depth order: swap the depths of close neighbours among the sorted
        candidates Fs (core and first excluded candidate). */
     const int64_t K = prm->K;
-    for (int64_t i = 0; i + 1 < Fs->n && i < K; ++i) {
+    for (int64_t i = 0; hybrid && i + 1 < Fs->n && i < K; ++i) {
         const og_frag *a = &Fs->f[i], *b = &Fs->f[i + 1];
         if (fabs(b->z - a->z) > OG_DEPTH_REL * fabs(a->z)) continue;
         const int32_t bit = (i + 1 == K) ? OG_AMB_CORE_EDGE : OG_AMB_CORE_TIE;
-        if (amb & bit) continue;
         work->n = 0;
         for (int64_t k = 0; k < F0->n; ++k) {
             og_frag f = F0->f[k];
@@ -730,9 +748,58 @@ static int32_t og_effects(const og_fragvec *F0, const og_fragvec *Bd, const og_f
             og_push(work, &f);
         }
         og_blend_copy(work->f, work->n, scratch, prm, &alt);
-        /* Equal depths after the swap are ordered by gid; make the swap strict. */
-        if (og_moves(&alt, res)) amb |= bit;
+        sum += (mv = og_move(&alt, res));
+        if (mv > OG_EFFECT_TOL) amb |= bit;
     }
+    if (budget) *budget = sum;
+    return amb;
+}
+
+/* Sorted blending (Tab. 3 variant): re-blends with each near-decision
+   flipped alone, the stop at a fragment whose T (1 - alpha) lies within
+   rounding of the threshold, and the order of two fragments (among the
+   blended ones and the first one left out) whose mean depths are within
+   OG_DEPTH_REL. Fs holds the fragments in blending order. */
+static int32_t og_effects_sorted(const og_fragvec *F0, const og_fragvec *Fs, int64_t used,
+                                 const og_pixel_result *res, const og_params *prm, og_fragvec *work,
+                                 og_fragvec *scratch, double *budget) {
+    int32_t amb = 0;
+    double sum = 0, mv;
+    og_pixel_result alt;
+    double T = 1.0;
+    const int64_t last = used < Fs->n ? used : Fs->n - 1;
+    for (int64_t i = 0; i <= last; ++i) {
+        const og_frag *f = &Fs->f[i];
+        const double Tn = T * (1.0 - f->alpha);
+        if (fabs(Tn - OG_SORTED_TMIN) <= 1e-6 * OG_SORTED_TMIN + 1e-7 * T) {
+            work->n = 0;
+            for (int64_t k = 0; k < F0->n; ++k) {
+                og_frag g = F0->f[k];
+                if (g.gid == f->gid) g.force = i < used ? -1 : 1;
+                og_push(work, &g);
+            }
+            og_blend_copy(work->f, work->n, scratch, prm, &alt);
+            sum += (mv = og_move(&alt, res));
+            if (mv > OG_EFFECT_TOL) amb |= OG_AMB_TERM;
+        }
+        if (i > 0 && fabs(f->zmean - Fs->f[i - 1].zmean) <= OG_DEPTH_REL * fabs(f->zmean)) {
+            const og_frag *a = &Fs->f[i - 1];
+            work->n = 0;
+            for (int64_t k = 0; k < F0->n; ++k) {
+                og_frag g = F0->f[k];
+                /* Swap the two mean depths; equal ones would fall back to the
+                   gid order, so the swap is made strict by the gids too. */
+                if (g.gid == a->gid) { g.zmean = f->zmean; g.gid = f->gid; }
+                else if (g.gid == f->gid) { g.zmean = a->zmean; g.gid = a->gid; }
+                og_push(work, &g);
+            }
+            og_blend_copy(work->f, work->n, scratch, prm, &alt);
+            sum += (mv = og_move(&alt, res));
+            if (mv > OG_EFFECT_TOL) amb |= OG_AMB_ORDER;
+        }
+        T = Tn;
+    }
+    if (budget) *budget = sum;
     return amb;
 }
 
@@ -748,8 +815,15 @@ static void og_render_task(void *vctx, int64_t b, int64_t e) {
         memset(&res, 0, sizeof(res));
         F.n = 0;
         Bd.n = 0;
-        for (int64_t g = 0; g < c->n; ++g) {
+        const int64_t n_test = c->idx ? c->n_idx : c->n;
+        for (int64_t t = 0; t < n_test; ++t) {
+            const int64_t g = c->idx ? c->idx[t] : t;
             if (!c->sp[g].valid) continue;
+            if (c->grown) {
+                const int64_t *q = c->grown + 4 * t;
+                const int64_t px = c->win.x0 + li, py = c->win.y0 + lj;
+                if (px < q[0] || px > q[1] || py < q[2] || py > q[3]) continue;
+            }
             og_frag fr;
             int border = 0;
             int kept = og_fragment(&c->sp[g], g, xs, ys, c->prm, &fr, &res.amb, &border);
@@ -769,9 +843,23 @@ static void og_render_task(void *vctx, int64_t b, int64_t e) {
             int64_t nc = 0;
             while (nc < F.n && (F.f[nc].force > 0 || (F.f[nc].force == 0 && F.f[nc].alpha >= c->prm->tau_K))) ++nc;
             Fs.n = nc < K + 1 ? nc : K + 1;
-            int32_t amb = near & (OG_AMB_DEN | OG_AMB_TERM | OG_AMB_ORDER);
-            if (near & (OG_AMB_CUTOFF | OG_AMB_TAUK | OG_AMB_CORE_EDGE | OG_AMB_CORE_TIE))
-                amb |= og_effects(&F0, &Bd, &Fs, &res, c->prm, &work, &scratch);
+            int32_t amb = near & OG_AMB_DEN;
+            double budget = 0, b2 = 0;
+            if (c->prm->sorted_blend) {
+                /* Blending order = the front of F after og_blend; the cutoff
+                   flips are evaluated like the hybrid ones. */
+                og_fragvec Fo = {F.f, F.n, 0};
+                if (near & (OG_AMB_TERM | OG_AMB_ORDER))
+                    amb |= og_effects_sorted(&F0, &Fo, res.n_core, &res, c->prm, &work, &scratch, &b2);
+                if (near & OG_AMB_CUTOFF) {
+                    og_fragvec none = {NULL, 0, 0};
+                    amb |= og_effects(&F0, &Bd, &none, &res, c->prm, &work, &scratch, &budget);
+                }
+                budget += b2;
+            } else if (near & (OG_AMB_CUTOFF | OG_AMB_TAUK | OG_AMB_CORE_EDGE | OG_AMB_CORE_TIE)) {
+                amb |= og_effects(&F0, &Bd, &Fs, &res, c->prm, &work, &scratch, &budget);
+            }
+            if (d->amb_effect) d->amb_effect[pix] = budget;
             if (d->n_frag) d->n_frag[pix] = (int32_t)res.n_frag;
             if (d->n_core) d->n_core[pix] = (int32_t)res.n_core;
             if (d->core_gid)
@@ -807,7 +895,7 @@ static int og_check(const og_camera *cam, const og_params *prm, const og_window 
 int og_render_splats(const og_splat *sp, int64_t n, const og_camera *cam, const og_params *prm,
                      const og_window *win, double *image, og_pixel_diag *diag) {
     if (og_check(cam, prm, win) || !image || (n > 0 && !sp)) return 1;
-    og_render_ctx c = {sp, n, cam, prm, *win, image, diag, 0};
+    og_render_ctx c = {sp, n, cam, prm, *win, image, diag, 0, NULL, 0, NULL};
     og_parallel_for((int64_t)win->w * win->h, 4, og_render_task, &c);
     return c.err ? 2 : 0;
 }
@@ -820,6 +908,54 @@ int og_render(const og_gaussians *g, const og_camera *cam, const og_params *prm,
     int rc = og_preprocess(g, cam, prm, sp);
     if (!rc) rc = og_render_splats(sp, g->n, cam, prm, win, image, diag);
     free(sp);
+    return rc;
+}
+
+/* og_render restricted to the Gaussians whose covered pixel rectangle, grown
+   by `margin` pixels on every side, meets the window. The tight box of
+   Sec. 3.2 contains every pixel centre with rho^2 <= rho_c, so the result
+   equals og_render's whenever the margin also covers the band of rejected
+   pairs within OG_CUTOFF_REL of the cutoff (a relative width of 1e-5 in
+   rho, i.e. less than a pixel for splats under 10^5 pixels across). Gids
+   keep their numbering in the full array. This only skips pairs that the
+   brute force would reject; the test suite checks equality with og_render. */
+int og_render_boxed(const og_gaussians *g, const og_camera *cam, const og_params *prm,
+                    const og_window *win, int32_t margin, double *image, og_pixel_diag *diag,
+                    int64_t *n_tested) {
+    if (!g || og_check(cam, prm, win) || !image || margin < 0) return 1;
+    og_splat *sp = (og_splat *)malloc((size_t)(g->n > 0 ? g->n : 1) * sizeof(og_splat));
+    int64_t *idx = (int64_t *)malloc((size_t)(g->n > 0 ? g->n : 1) * sizeof(int64_t));
+    int64_t *grown = (int64_t *)malloc((size_t)(g->n > 0 ? g->n : 1) * 4 * sizeof(int64_t));
+    if (!sp || !idx || !grown) { free(sp); free(idx); free(grown); return 2; }
+    int rc = og_preprocess(g, cam, prm, sp);
+    int64_t m = 0;
+    if (!rc) {
+        const int64_t wx0 = win->x0, wx1 = (int64_t)win->x0 + win->w - 1;
+        const int64_t wy0 = win->y0, wy1 = (int64_t)win->y0 + win->h - 1;
+        for (int64_t i = 0; i < g->n; ++i) {
+            const og_splat *q = &sp[i];
+            if (!q->valid) continue;
+            /* The rectangle is clamped to the image; a splat whose box lies
+               off-image has an empty one but may still border the window
+               across the image edge, so the clamped sides are widened too. */
+            int64_t x0 = q->rect[0], x1 = q->rect[1], y0 = q->rect[2], y1 = q->rect[3];
+            const double bx0 = floor(q->p[0] - q->h[0] - 0.5), bx1 = ceil(q->p[0] + q->h[0] - 0.5);
+            const double by0 = floor(q->p[1] - q->h[1] - 0.5), by1 = ceil(q->p[1] + q->h[1] - 0.5);
+            if (x0 > x1) { x0 = bx0 < -1e9 ? -1000000000 : (int64_t)bx0; x1 = bx1 > 1e9 ? 1000000000 : (int64_t)bx1; }
+            if (y0 > y1) { y0 = by0 < -1e9 ? -1000000000 : (int64_t)by0; y1 = by1 > 1e9 ? 1000000000 : (int64_t)by1; }
+            if (x1 + margin < wx0 || x0 - margin > wx1 || y1 + margin < wy0 || y0 - margin > wy1) continue;
+            grown[4 * m + 0] = x0 - margin; grown[4 * m + 1] = x1 + margin;
+            grown[4 * m + 2] = y0 - margin; grown[4 * m + 3] = y1 + margin;
+            idx[m++] = i;
+        }
+        og_render_ctx c = {sp, g->n, cam, prm, *win, image, diag, 0, idx, m, grown};
+        og_parallel_for((int64_t)win->w * win->h, 4, og_render_task, &c);
+        rc = c.err ? 2 : 0;
+    }
+    if (n_tested) *n_tested = m;
+    free(sp);
+    free(idx);
+    free(grown);
     return rc;
 }
 
