@@ -28,7 +28,7 @@ TAU_A = 1.0 / 255.0
 W = H = 16
 FX = 16.0
 CX = CY = 8.5   # the ray through pixel (8, 8) is the optical axis
-CUT_REL, TAUK_ABS, AMAX_ABS, DEPTH_REL, EFFECT = 2e-5, 2e-6, 1e-6, 1e-5, 2e-5
+CUT_REL, TAUK_ABS, AMAX_ABS, DEPTH_REL, EFFECT = 2e-5, 2e-6, 1e-6, 1e-6, 2e-5
 Y00 = 0.5 / math.sqrt(math.pi)
 
 
@@ -204,14 +204,14 @@ def test_alpha_clamp_is_near_but_never_ambiguous():
 
 @pytest.mark.parametrize("same_colour", [False, True])
 def test_core_edge_tie(same_colour):
-    """K = 1 and two splats whose depths differ by 4e-6 (relative) on every
+    """K = 1 and two splats whose depths differ by 4e-7 (relative) on every
     ray: wherever both are core candidates the K-th and (K+1)-th candidate
-    depths are within the oracle's 1e-5 margin (edge bit). Swapping them
+    depths are within the oracle's 1e-6 margin (edge bit). Swapping them
     moves the colour by alpha_A alpha_B (c_A - c_B), zero for equal colours."""
     ca = np.array([1.0, 0.2, 0.0])
     cb = ca if same_colour else np.array([0.0, 0.4, 1.0])
     A = ((0.0, 0.0, 3.0), 0.3, 0.5, tuple(ca))
-    Bs = ((0.0, 0.0, 3.0 * (1 + 4e-6)), 0.3, 0.45, tuple(cb))
+    Bs = ((0.0, 0.0, 3.0 * (1 + 4e-7)), 0.3, 0.45, tuple(cb))
     img, d, prm = _render([A, Bs], K=1)
     both = set()
     for j in range(H):
@@ -219,7 +219,7 @@ def test_core_edge_tie(same_colour):
             ra, za = _rho2_z(A[0], A[1], i, j)
             rb, zb = _rho2_z(Bs[0], Bs[1], i, j)
             aa, ab = A[2] * math.exp(-0.5 * ra), Bs[2] * math.exp(-0.5 * rb)
-            assert abs(zb - za) / za == pytest.approx(4e-6, rel=1e-3)
+            assert abs(zb - za) / za == pytest.approx(4e-7, rel=1e-3)
             if aa >= prm.tau_K and ab >= prm.tau_K:
                 both.add((i, j))
                 expect = aa * ab * np.abs(ca - cb).max()
@@ -237,7 +237,7 @@ def test_core_tie_inside_the_core_and_clear_gaps():
     a third splat far behind (no edge bit: its depth is 30% away)."""
     ca, cb, cc = np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])
     A = ((0.0, 0.0, 3.0), 0.3, 0.5, tuple(ca))
-    Bs = ((0.0, 0.0, 3.0 * (1 + 3e-6)), 0.3, 0.4, tuple(cb))
+    Bs = ((0.0, 0.0, 3.0 * (1 + 3e-7)), 0.3, 0.4, tuple(cb))
     C = ((0.0, 0.0, 4.0), 0.3, 0.7, tuple(cc))
     img, d, _ = _render([A, Bs, C], K=2)
     assert d["near_decision"][8, 8] == oracle.AMB_CORE_TIE
@@ -245,8 +245,8 @@ def test_core_tie_inside_the_core_and_clear_gaps():
     assert d["amb_effect"][8, 8] == pytest.approx(0.5 * 0.4 * 1.0, rel=1e-6)
     # Core (depth order) is A then B; the tail is C.
     assert list(d["core_gid"][8, 8]) == [0, 1]
-    # A 1e-3 gap is far outside the margin: nothing is flagged.
-    B2 = ((0.0, 0.0, 3.0 * (1 + 1e-3)), 0.3, 0.4, tuple(cb))
+    # A 1e-5 gap is outside the margin: nothing is flagged.
+    B2 = ((0.0, 0.0, 3.0 * (1 + 1e-5)), 0.3, 0.4, tuple(cb))
     img, d, _ = _render([A, B2, C], K=2)
     assert not d["near_decision"].any() and not d["ambiguous"].any()
 
@@ -307,11 +307,11 @@ def test_random_scene_flags_only_real_events():
 
 def test_sorted_blend_order_flip():
     """Mean-depth-sorted blending (Tab. 3 variant): two splats whose mean
-    depths differ by 4e-6 (relative). Their order is a near-decision; the
+    depths differ by 4e-7 (relative). Their order is a near-decision; the
     swap moves the colour by alpha_A alpha_B (c_A - c_B)."""
     ca, cb = np.array([1.0, 0.3, 0.0]), np.array([0.0, 0.3, 1.0])
     A = ((0.0, 0.0, 3.0), 0.3, 0.5, tuple(ca))
-    Bs = ((0.0, 0.0, 3.0 * (1 + 4e-6)), 0.3, 0.6, tuple(cb))
+    Bs = ((0.0, 0.0, 3.0 * (1 + 4e-7)), 0.3, 0.6, tuple(cb))
     img, d, _ = _render([A, Bs], sorted_blend=True)
     assert d["near_decision"][8, 8] & oracle.AMB_ORDER
     assert d["ambiguous"][8, 8] == oracle.AMB_ORDER

@@ -166,3 +166,24 @@ def test_densification_statistic_is_half_distance_times_mean_gradient():
     np.testing.assert_array_equal(out["densify_count"], covers.astype(float))
     want = np.where(covers, 0.5 * dist * np.linalg.norm(out["means"], axis=1), 0.0)
     np.testing.assert_allclose(out["densify_grad"], want, rtol=1e-12, atol=0)
+
+
+def test_config3_crop_central_differences():
+    """The training step's finite-difference check at its stated size: 64
+    Gaussians of the training distribution (SH degree 3, view dependence
+    boosted) seen through a 32x32 crop of the 1200x800, f = 1200 camera with
+    the principal point shifted, K = 8. Every one of the 64 x 59 parameters
+    (means, log-scales, quaternions, opacity logits, SH) is perturbed by
+    h = 1e-6 both ways in FP64; parameters whose perturbation changes a
+    discrete decision (fragment set, core membership or order) are skipped."""
+    scene = scenes.small_box_scene(64, seed=2, sh_degree=3).astype(np.float64)
+    scene.sh[:, 1:, :] *= 6.0
+    scene.means[:, :2] *= 0.04
+    cam = scenes.identity_camera(1200, 800, 1200.0).crop(584, 384, 32, 32)
+    assert (cam.cx, cam.cy) == (16.0, 16.0) and (cam.width, cam.height) == (32, 32)
+    prm = scenes.Params(K=8, bg=(0.1, 0.2, 0.3))
+    img, d = oracle.render(scene, cam, prm, diagnostics=True)
+    assert d["n_frag"].mean() > 8 and (d["n_frag"] > prm.K).mean() > 0.3  # core and tail both used
+    n_cmp, n_skip = _fd_check(scene, cam, prm, (0, 0, 32, 32), seed=3)
+    assert n_cmp + n_skip == 64 * 59
+    assert n_cmp > 0.9 * (n_cmp + n_skip), (n_cmp, n_skip)
