@@ -1,6 +1,8 @@
 """Shared helpers of the GPU parity tests (CUDA path vs the FP64 oracle)."""
 from __future__ import annotations
 
+import json
+
 import numpy as np
 import torch
 
@@ -11,10 +13,20 @@ from paper_2410_08129_gb300.renderer import FIELDS, GaussianTensors, Renderer
 
 # Per-channel tolerance of the image (FP32 path vs FP64 oracle).
 IMAGE_TOL = 2e-4
-# Largest share of pixels on which a near-decision (cutoff, tau_K, depth tie)
-# could flip between FP32 and FP64 and move the colour by more than 2e-5;
-# those pixels are excluded from the element-by-element comparison.
-MAX_AMBIGUOUS = 0.03
+TAU_ALPHA = 1.0 / 255.0
+# Default cap on the share of pixels holding a near-decision whose flip alone
+# moves the colour by more than 2e-5 (the oracle's `ambiguous`). Such pixels
+# are not skipped: each is held to IMAGE_TOL plus the oracle's per-pixel
+# budget (the sum of its single-flip colour moves). Workloads with deep
+# pixels reach more (in-core depth ties); those tests pass their own cap,
+# set from the oracle's measured fraction on that input.
+MAX_AMBIGUOUS = 1e-3
+# The oracle's near-decision margins (the FP32 path may take a decision the
+# other way only within them).
+DEPTH_REL, TAUK_ABS, CUTOFF_REL = 1e-6, 2e-6, 2e-5
+# Near-decisions without a per-pixel budget: a ray almost parallel to a flat
+# splat (its FP32 evaluation can return any alpha and depth).
+UNBOUNDED = oracle.AMB_DEN
 
 
 def gpu_render(scene, cam, params, tile=(16, 16), ppt=0, capacity=None, save=True):
@@ -54,21 +66,73 @@ def saved_planes(r: Renderer, cam, K):
 CORE_NEAR = oracle.AMB_CORE_TIE | oracle.AMB_CORE_EDGE | oracle.AMB_TAUK
 
 
-def assert_core_ids(sv, d):
-    """The core (integer work) equals the oracle's, ids in depth order, on
-    every pixel without an ambiguity and without a near-decision that could
-    change it; where the only such decision is a depth tie inside the core
-    (the order of nearly equal depths), both lists hold the same ids. Returns
-    the fraction of pixels compared exactly."""
+def assert_core_ids(sv, d, scene, cam, prm, window=None, label="core"):
+    """The K-core (integer work, Sec. 3.3: the K nearest candidates with
+    alpha >= tau_K in (z, gid) order) on every pixel of the window.
+
+    Pixels without an ambiguity and without a near-decision that can change
+    the core: ids and count identical to the oracle's. Every other pixel:
+    the GPU's list is re-evaluated in FP64 (rho^2, alpha, depth of each id)
+    and must be a correct core up to the oracle's margins: each entry a
+    candidate, depths in order except inversions within DEPTH_REL, and each
+    id where the two lists differ explained by a depth within DEPTH_REL of
+    the other list's last entry (a full core) or by an alpha within TAUK_ABS
+    of tau_K. Prints a CORE line with the share compared exactly and the
+    largest relative depth gap at which the GPU ordered two fragments
+    differently from the oracle; returns them."""
+    K = prm.K
+    x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
+    g_n = sv["n_core"][y0:y0 + h, x0:x0 + w]
+    g_ids = sv["core_gid"][y0:y0 + h, x0:x0 + w]
     amb = d["ambiguous"] != 0
     near = d["near_decision"] & CORE_NEAR
-    ok = ~amb & (near == 0)
-    np.testing.assert_array_equal(sv["n_core"][ok], d["n_core"][ok])
-    np.testing.assert_array_equal(sv["core_gid"][ok], d["core_gid"][ok])
-    tie = ~amb & (near == oracle.AMB_CORE_TIE)
-    np.testing.assert_array_equal(sv["n_core"][tie], d["n_core"][tie])
-    np.testing.assert_array_equal(np.sort(sv["core_gid"][tie], -1), np.sort(d["core_gid"][tie], -1))
-    return float(ok.mean())
+    exact = ~amb & (near == 0)
+    np.testing.assert_array_equal(g_n[exact], d["n_core"][exact])
+    np.testing.assert_array_equal(g_ids[exact], d["core_gid"][exact])
+    differ = ~exact & ((g_n != d["n_core"]) | np.any(g_ids != d["core_gid"], axis=-1))
+    sp = oracle.preprocess(scene.astype(np.float64), cam, prm) if differ.any() else None
+    worst_gap = 0.0
+    for j, i in zip(*np.nonzero(differ)):
+        xs, ys = x0 + i + 0.5, y0 + j + 0.5
+        G = [int(v) for v in g_ids[j, i, :g_n[j, i]]]
+        O = [int(v) for v in d["core_gid"][j, i, :d["n_core"][j, i]]]
+        ev = {}
+        for gid in set(G) | set(O):
+            hit, rho2, z, a_raw, _, _ = oracle.eval_pair(sp, gid, xs, ys)
+            rc = sp["rho_c"][gid]
+            alpha = min(a_raw, prm.alpha_max)
+            assert sp["valid"][gid] and hit and rho2 <= rc + CUTOFF_REL * max(1.0, rc), (label, i, j, gid)
+            assert alpha >= prm.tau_K - TAUK_ABS, (label, i, j, gid, alpha)
+            ev[gid] = (z, abs(alpha - prm.tau_K) <= TAUK_ABS)
+        zg = [ev[g][0] for g in G]
+        for a, b in zip(zg, zg[1:]):
+            if b < a:
+                gap = (a - b) / abs(a)
+                worst_gap = max(worst_gap, gap)
+                assert gap <= DEPTH_REL, (label, i, j, G, zg)
+        only_g, only_o = set(G) - set(O), set(O) - set(G)
+        zo_last = ev[O[-1]][0] if O else None
+        zg_last = zg[-1] if G else None
+        for gid in only_g:
+            z, at_tau = ev[gid]
+            if at_tau:
+                continue
+            assert len(O) == K and zo_last is not None, (label, i, j, G, O)
+            gap = (z - zo_last) / abs(zo_last)
+            worst_gap = max(worst_gap, gap)
+            assert gap <= DEPTH_REL, (label, i, j, G, O, gap)
+        for gid in only_o:
+            z, at_tau = ev[gid]
+            if at_tau:
+                continue
+            assert len(G) == K and zg_last is not None, (label, i, j, G, O)
+            gap = (zg_last - z) / abs(zg_last)
+            worst_gap = max(worst_gap, gap)
+            assert gap <= DEPTH_REL, (label, i, j, G, O, gap)
+    rep = dict(label=label, exact=float(exact.mean()), differ=int(differ.sum()),
+               worst_depth_gap=worst_gap)
+    print("CORE " + json.dumps(rep))
+    return rep
 
 
 def workspace_view(r: Renderer, offset, count, dtype):
@@ -76,34 +140,77 @@ def workspace_view(r: Renderer, offset, count, dtype):
     return r.workspace[offset: offset + count * itemsize].view(dtype)
 
 
-def compare_images(img, ref, amb, tol=IMAGE_TOL):
-    """Returns (max error on unambiguous pixels, ambiguous fraction, max error on ambiguous pixels)."""
+def image_parity(img, ref, d, label, max_ambiguous=MAX_AMBIGUOUS, tol=IMAGE_TOL, max_colour=1.0):
+    """Element-by-element image parity with the FP64 oracle (Eq. (15)).
+
+    - Pixels without an ambiguous near-decision: every channel within tol.
+    - Ambiguous pixels: within tol + the oracle's amb_effect for that pixel
+      (the FP32 path may take any of its near-decisions the other way, each
+      moving the colour by at most its measured single-flip move); those
+      whose only colour-moving decisions are at the cutoff are also within
+      tau_alpha * max_colour + tol (a fragment at the cutoff has alpha =
+      tau_alpha).
+    - Pixels with a near-decision that has no budget (a ray grazing a flat
+      splat) are at most 0.1% and finite.
+    - The ambiguous share is at most max_ambiguous.
+    Prints one PARITY line with the measured figures and returns them."""
+    img = np.asarray(img, np.float64)
+    assert img.shape == ref.shape, (img.shape, ref.shape)
+    assert np.isfinite(img).all(), label
     err = np.abs(img - ref).max(-1)
+    amb = d["ambiguous"]
     ok = amb == 0
+    unb = (amb & UNBOUNDED) != 0
+    bounded = ~ok & ~unb
+    budget = d["amb_effect"]
     e_ok = float(err[ok].max()) if ok.any() else 0.0
-    e_amb = float(err[~ok].max()) if (~ok).any() else 0.0
-    return e_ok, float((~ok).mean()), e_amb
+    ratio = err[bounded] / (tol + budget[bounded])
+    cut_only = bounded & (amb == oracle.AMB_CUTOFF)
+    rep = dict(label=label, pixels=int(err.size), err=e_ok, ambiguous=float((~ok).mean()),
+               n_ambiguous=int((~ok).sum()), flipped=float((err > tol).mean()),
+               e_amb=float(err[~ok].max()) if (~ok).any() else 0.0,
+               worst_budget_ratio=float(ratio.max()) if ratio.size else 0.0,
+               e_cut_only=float(err[cut_only].max()) if cut_only.any() else 0.0,
+               unbounded=float(unb.mean()))
+    print("PARITY " + json.dumps(rep))
+    assert e_ok <= tol, rep
+    if ratio.size:
+        k = int(np.argmax(ratio))
+        jj, ii = np.nonzero(bounded)
+        assert ratio[k] <= 1.0, dict(rep, pixel=(int(ii[k]), int(jj[k])), bits=int(amb[jj[k], ii[k]]),
+                                     budget=float(budget[jj[k], ii[k]]))
+    assert rep["e_cut_only"] <= TAU_ALPHA * max_colour + tol, rep
+    assert rep["unbounded"] <= 1e-3, rep
+    assert rep["ambiguous"] <= max_ambiguous, rep
+    return rep
 
 
-def crop_compare(scene, cam, params, window, img_full, sp=None):
+def crop_parity(scene, cam, params, window, img_full, label, max_ambiguous=MAX_AMBIGUOUS, box_margin=2):
+    """image_parity on a window of a full-frame GPU image; the oracle tests
+    the window against the Gaussians whose FP64 box (grown by box_margin
+    pixels) meets each pixel, which equals its brute force."""
     x0, y0, w, h = window
-    ref, d = oracle.render(scene.astype(np.float64), cam, params, window=window, diagnostics=True)
+    ref, d = oracle.render(scene.astype(np.float64), cam, params, window=window, diagnostics=True,
+                           box_margin=box_margin)
     sub = img_full[y0:y0 + h, x0:x0 + w]
-    return compare_images(sub, ref, d["ambiguous"]), ref, d
+    return image_parity(sub, ref, d, label, max_ambiguous), ref, d
 
 
 def grads_to_numpy(grads):
     return {f: grads[f].detach().cpu().numpy().astype(np.float64) for f in FIELDS}
 
 
-def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, floor=1e-2, names=FIELDS):
+def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, floor=1e-3, names=FIELDS, label="grad"):
     """Per tensor: ||g - ref|| <= rel_norm ||ref||, and elementwise
     |g - ref| <= rel_elem * max(|ref|, floor * max|ref|) (+ a floor for
-    all-zero tensors). The elementwise floor reflects FP32 accumulation: an
+    all-zero tensors), the reading of "1e-3 relative" used throughout. An
     element is a sum over pixels whose terms can be as large as the tensor's
-    largest entry and cancel, so its absolute error scales with max|ref|,
-    not with its own (possibly tiny) value."""
-    report = {}
+    largest entry and cancel, so its FP32 error scales with max|ref|, not with
+    its own (possibly tiny) value: the floor keeps elements near zero from
+    being held to a relative bound below FP32 accumulation error. Prints a
+    GRAD line with each tensor's relative norm error and worst elementwise
+    ratio (at this floor)."""
+    report, details = {}, []
     for f in names:
         a, b = g[f].reshape(-1), ref[f].reshape(-1)
         nb = np.linalg.norm(b)
@@ -111,12 +218,15 @@ def assert_grad_close(g, ref, rel_norm=1e-3, rel_elem=1e-3, floor=1e-2, names=FI
         if nb == 0:
             assert np.abs(a).max() <= 1e-6, (f, np.abs(a).max())
             continue
-        rn = np.linalg.norm(a - b) / nb
-        bound = rel_elem * np.maximum(np.abs(b), floor * mx) + 1e-9
-        worst = float(np.max(np.abs(a - b) / bound))
-        report[f] = (rn, worst)
-        k = int(np.argmax(np.abs(a - b) / bound))
-        detail = dict(field=f, rel_norm=rn, worst=worst, index=k, got=float(a[k]), want=float(b[k]), max_abs=mx)
-        assert rn <= rel_norm, detail
-        assert worst <= 1.0, detail
+        rn = float(np.linalg.norm(a - b) / nb)
+        ratio = np.abs(a - b) / (rel_elem * np.maximum(np.abs(b), floor * mx) + 1e-9)
+        k = int(np.argmax(ratio))
+        report[f] = (rn, float(ratio[k]))
+        details.append(dict(field=f, rel_norm=rn, worst=float(ratio[k]), index=k, got=float(a[k]),
+                            want=float(b[k]), max_abs=float(mx)))
+    print("GRAD " + json.dumps(dict(label=label, floor=floor,
+                                    **{k: [v[0], v[1]] for k, v in report.items()})))
+    for dt in details:
+        assert dt["rel_norm"] <= rel_norm, dt
+        assert dt["worst"] <= 1.0, dt
     return report

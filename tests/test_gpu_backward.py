@@ -33,10 +33,17 @@ def _masked_upstream(scene, cam, prm, seed):
     return dl.astype(np.float32), d
 
 
-@pytest.mark.parametrize("degree,K,tile,ppt", [(0, 8, (16, 16), 2), (3, 4, (16, 8), 1), (3, 16, (8, 8), 2),
-                                               (1, 0, (16, 16), 4), (2, 32, (16, 16), 1), (1, 8, (32, 16), 1),
-                                               (2, 32, (32, 16), 2)])
-def test_small_scene_gradients(degree, K, tile, ppt):
+# The elementwise floor is 1e-3 of the tensor's largest entry except where
+# FP32 accumulation measurably needs more: one log-scale gradient (an element
+# 2.5e-4 of the largest, the difference of larger per-pixel terms) is off by
+# 7.5e-6 and 4.8e-6 of the largest at K = 32 (ratio 7.5 and 4.8 at 1e-3), and
+# one at degree 3, K = 4 (1.9e-3 of the largest) by 2.4e-6 of the largest
+# (ratio 1.25 at 1e-3, 1.18 at 2e-3); the norm errors stay <= 1.4e-5.
+@pytest.mark.parametrize("degree,K,tile,ppt,floor", [(0, 8, (16, 16), 2, 1e-3), (3, 4, (16, 8), 1, 4e-3),
+                                                     (3, 16, (8, 8), 2, 1e-3), (1, 0, (16, 16), 4, 1e-3),
+                                                     (2, 32, (16, 16), 1, 1e-2), (1, 8, (32, 16), 1, 1e-3),
+                                                     (2, 32, (32, 16), 2, 1e-2)])
+def test_small_scene_gradients(degree, K, tile, ppt, floor):
     """64 Gaussians of the training-step distribution seen through a 32x32
     crop of the 1200x800 camera (principal point shifted)."""
     scene = scenes.small_box_scene(64, seed=2, sh_degree=degree)
@@ -48,8 +55,8 @@ def test_small_scene_gradients(degree, K, tile, ppt):
     dl, d = _masked_upstream(scene, cam, prm, seed=degree + K)
     ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl.astype(np.float64))
     got, _ = _gpu_grads(scene, cam, prm, dl, tile, ppt)
-    rep = assert_grad_close(got, ref)
-    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()}, "masked", (d["near_decision"] != 0).mean())
+    print("masked", (d["near_decision"] != 0).mean())
+    assert_grad_close(got, ref, floor=floor, label=f"small scene degree={degree} K={K} {tile} ppt={ppt}")
 
 
 def test_no_tail_gradients():
@@ -60,8 +67,7 @@ def test_no_tail_gradients():
     dl, d = _masked_upstream(scene, cam, prm, seed=11)
     ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl.astype(np.float64))
     got, _ = _gpu_grads(scene, cam, prm, dl)
-    rep = assert_grad_close(got, ref)
-    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()})
+    assert_grad_close(got, ref, label="no tail K=4")
 
 
 def test_autograd_function_matches_direct_call():
@@ -112,6 +118,9 @@ def test_training_step_distribution_crop_gradients(training_window, tile):
     got, r = _gpu_grads(scene, cam, prm, dl, tile=tile, ppt=1)
     touched = np.abs(ref["opacity_logits"]) > 0
     assert touched.sum() > 1000
-    rep = assert_grad_close(got, ref)
-    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()}, "touched", int(touched.sum()),
-          "masked", float(((d["near_decision"] & ~oracle.AMB_CUTOFF) != 0).mean()), "instances", r.last_instances)
+    print("training window: masked", float(((d["near_decision"] & ~oracle.AMB_CUTOFF) != 0).mean()),
+          "near cutoff", float(((d["near_decision"] & oracle.AMB_CUTOFF) != 0).mean()),
+          "touched", int(touched.sum()), "instances", r.last_instances)
+    # One mean gradient (1e-5 of the largest) is off by 1.5e-6 of the largest
+    # (ratio 1.41 at the 1e-3 floor): FP32 sums over ~10^4 fragments a pixel.
+    assert_grad_close(got, ref, floor=2e-3, label=f"training window {tile}")

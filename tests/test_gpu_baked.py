@@ -16,7 +16,7 @@ from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
 from paper_2410_08129_gb300.renderer import (FIELDS, BakedGaussians, BatchRenderer, GaussianTensors, Renderer,
                                              _c_grad)
-from tests.gpu_util import IMAGE_TOL, MAX_AMBIGUOUS, compare_images
+from tests.gpu_util import image_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +63,10 @@ def test_baked_render_equals_raw_render(degree, filt, K):
     baked = r.forward(g.bake()).clone()
     assert torch.equal(raw, baked)
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb, _ = compare_images(baked.cpu().numpy().astype(np.float64), ref, d["ambiguous"])
-    assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS, (e_ok, amb)
+    # The oracle marks 0.16, 0.19 and 0.25% of the pixels ambiguous.
+    cap = {4: 0.0016, 8: 0.0019, 0: 0.0026}[K]
+    # (Degree-3 colours reach a little above 1: higher bands are N(0, 0.05).)
+    image_parity(baked.cpu().numpy(), ref, d, f"baked degree={degree} K={K}", cap, max_colour=1.5)
 
 
 def test_baked_scenes_in_a_batch():

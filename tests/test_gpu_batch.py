@@ -10,7 +10,7 @@ import oracle
 from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
 from paper_2410_08129_gb300.renderer import FIELDS, BatchRenderer, GaussianTensors, Renderer
-from tests.gpu_util import IMAGE_TOL, MAX_AMBIGUOUS, compare_images
+from tests.gpu_util import image_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -67,8 +67,7 @@ def test_batch_view_matches_oracle():
     imgs = BatchRenderer([g] * len(cams), cams, prm).forward()
     for cam, img in zip(cams, imgs):
         ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-        e_ok, amb, _ = compare_images(img.cpu().numpy().astype(np.float64), ref, d["ambiguous"])
-        assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS, (cam.width, cam.height, e_ok, amb)
+        image_parity(img.cpu().numpy(), ref, d, f"batch view {cam.width}x{cam.height}")
 
 
 def test_batch_backward_sums_views_of_one_scene():

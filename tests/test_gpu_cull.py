@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
-from tests.gpu_util import IMAGE_TOL, MAX_AMBIGUOUS, compare_images, gpu_render
+from tests.gpu_util import gpu_render, image_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -60,8 +60,9 @@ def test_thin_splats_match_the_oracle(thin):
     scene, cam, prm, runs = thin
     img, counters = runs[SHAPES[0]]
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb, _ = compare_images(img, ref, d["ambiguous"])
-    assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS, (e_ok, amb)
+    # The oracle marks 0.29% of the pixels ambiguous (mostly cutoff decisions
+    # of needles and discs).
+    image_parity(img, ref, d, "thin splats", 0.0029)
     # Every fragment the oracle keeps is kept (up to cutoff decisions that
     # FP32 and FP64 take differently, a few per million).
     n_ref = int(d["n_frag"].sum())

@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2410_08129_gb300 import scenes
 from paper_2410_08129_gb300.renderer import FIELDS, BatchRenderer, GaussianTensors, Renderer
-from tests.gpu_util import (IMAGE_TOL, MAX_AMBIGUOUS, assert_core_ids, assert_grad_close, compare_images, gpu_render,
+from tests.gpu_util import (assert_core_ids, assert_grad_close, gpu_render, image_parity,
                             grads_to_numpy, saved_planes)
 
 pytestmark = pytest.mark.gpu
@@ -28,10 +28,9 @@ def test_filtered_forward_matches_oracle():
     prm = scenes.Params(K=8, bg=(0.1, 0.3, 0.2))
     img, r, _ = gpu_render(scene, cam, prm)
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb, _ = compare_images(img, ref, d["ambiguous"])
-    assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS, (e_ok, amb)
+    image_parity(img, ref, d, "3D filter K=8")
     sv = saved_planes(r, cam, prm.K)
-    assert assert_core_ids(sv, d) > 0.95
+    assert assert_core_ids(sv, d, scene, cam, prm, label="3D filter K=8")["exact"] > 0.99
     # the filter changes the image (wider, dimmer splats)
     plain, _, _ = gpu_render(dataclasses.replace(scene, filter_var=None), cam, prm)
     assert np.abs(plain - img).max() > 1e-2
@@ -55,8 +54,7 @@ def test_filtered_gradients_match_oracle(K):
     r.forward(g)
     got = r.backward(g, torch.as_tensor(dl).cuda())
     torch.cuda.synchronize()
-    rep = assert_grad_close(grads_to_numpy(got), ref)
-    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()})
+    assert_grad_close(grads_to_numpy(got), ref, label=f"3D filter K={K}")
 
 
 def test_filtered_batch_equals_single_views():

@@ -11,8 +11,7 @@ import oracle
 from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
 from paper_2410_08129_gb300.renderer import GaussianTensors, Renderer
-from tests.gpu_util import (IMAGE_TOL, MAX_AMBIGUOUS, assert_core_ids, compare_images, gpu_render, saved_planes,
-                            workspace_view)
+from tests.gpu_util import assert_core_ids, gpu_render, image_parity, saved_planes, workspace_view
 
 pytestmark = pytest.mark.gpu
 
@@ -28,19 +27,15 @@ def cfg1():
 
 def test_config1_image_parity(cfg1):
     scene, cam, prm, tile, img, r, g, ref, d = cfg1
-    e_ok, amb_frac, e_amb = compare_images(img, ref, d["ambiguous"])
-    print(f"config1: max err {e_ok:.3e} on unambiguous pixels, ambiguous {amb_frac:.4f} (max err {e_amb:.3e})")
-    assert np.isfinite(img).all()
-    assert e_ok <= IMAGE_TOL
-    assert amb_frac <= MAX_AMBIGUOUS
+    image_parity(img, ref, d, "config1 K=4")
 
 
 def test_config1_core_ids_match(cfg1):
     """The K-core (ids in depth order) is integer work: identical on every
-    pixel without a near-decision."""
+    pixel without a near-decision, valid within the margins on the others."""
     scene, cam, prm, tile, img, r, g, ref, d = cfg1
     sv = saved_planes(r, cam, prm.K)
-    assert assert_core_ids(sv, d) > 0.95
+    assert assert_core_ids(sv, d, scene, cam, prm, label="config1")["exact"] > 0.99
     ok = d["ambiguous"] == 0
     # T_core per pixel (FP32 vs FP64)
     assert np.abs(sv["T_core"][ok] - d["T_core"][ok]).max() <= 1e-5
@@ -126,9 +121,11 @@ def test_k_values(K):
     prm = scenes.Params(K=K, bg=(0.2, 0.3, 0.4))
     img, r, g = gpu_render(scene, cam, prm)
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb_frac, e_amb = compare_images(img, ref, d["ambiguous"])
-    print(f"K={K}: err {e_ok:.3e} amb {amb_frac:.4f} ({e_amb:.3e}), frags/px max {d['n_frag'].max()}")
-    assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS
+    # Oracle's ambiguous share on this input: 0.07, 0.09, 0.09, 0.11, 0.11%.
+    cap = {0: 1e-3, 1: 1e-3, 8: 1e-3, 16: 0.0012, 32: 0.0012}[K]
+    image_parity(img, ref, d, f"k_values K={K}", cap)
+    if K:
+        assert_core_ids(saved_planes(r, cam, K), d, scene, cam, prm, label=f"k_values K={K}")
 
 
 @pytest.mark.parametrize("K", [4, 16])
@@ -140,10 +137,9 @@ def test_no_tail_matches_oracle(K):
     prm = scenes.Params(K=K, bg=(0.2, 0.3, 0.4), no_tail=True)
     img, r, g = gpu_render(scene, cam, prm)
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb_frac, _ = compare_images(img, ref, d["ambiguous"])
-    assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS, (e_ok, amb_frac)
+    image_parity(img, ref, d, f"no_tail K={K}")
     sv = saved_planes(r, cam, K)
-    assert assert_core_ids(sv, d) > 0.95
+    assert assert_core_ids(sv, d, scene, cam, prm, label=f"no_tail K={K}")["exact"] > 0.99
     assert np.all(sv["A_tail"] == 0.0)
     with_tail, *_ = gpu_render(scene, cam, scenes.Params(K=K, bg=(0.2, 0.3, 0.4)))
     assert np.abs(with_tail - img).max() > 1e-3
@@ -193,8 +189,7 @@ def test_ragged_image_and_big_splats():
     for tile in [(16, 16), (32, 16), (16, 8), (8, 8)]:
         img, r, g = gpu_render(scene, cam, prm, tile=tile)
         ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-        e_ok, amb_frac, _ = compare_images(img, ref, d["ambiguous"])
-        assert e_ok <= IMAGE_TOL and amb_frac <= MAX_AMBIGUOUS, (tile, e_ok, amb_frac)
+        image_parity(img, ref, d, f"ragged {tile}")
 
 
 def test_empty_and_culled_scenes():
@@ -222,8 +217,8 @@ def test_overflow_is_reported_and_recovered():
     assert dev == B.HTGS_ERR_OVERFLOW and inst > 16
     img2 = r.forward(g)           # grows the workspace and re-renders
     assert r.last_instances == inst
-    ref = oracle.render(scene.astype(np.float64), cam, prm)
-    assert np.abs(img2.cpu().numpy() - ref).max() < 0.05
+    ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    image_parity(img2.cpu().numpy(), ref, d, "overflow recovered")
 
 
 def test_invalid_arguments_rejected():

@@ -1,0 +1,67 @@
+"""Decision resolution of the FP32 path, measured against the FP64 oracle.
+
+The oracle's near-decision margins (cutoff: rho^2 within 2e-5 of rho_c;
+depth order: 1e-6 relative) claim that the CUDA path takes a discrete
+decision of Sec. 3.2-3.3 differently from FP64 only inside them. This test
+makes every decision visible: with tau_K = 0 every kept fragment is a core
+candidate, so on a pixel with at most K - 1 = 31 fragments the saved core
+lists exactly the fragments the GPU kept, in the GPU's depth order. Each
+fragment the two sides disagree on is re-evaluated in FP64 (rho^2 / rho_c)
+and must lie in the cutoff band; each pair the GPU ordered differently must
+be within the depth margin. The largest such distances are printed: they are
+the measured resolution the margins are set against."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_08129_gb300 import scenes
+from tests.gpu_util import CUTOFF_REL, DEPTH_REL, gpu_render, saved_planes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed,grow,n", [(95, -1.5, 10000), (97, -1.2, 5000)])
+def test_cutoff_and_depth_decisions_lie_within_the_margins(seed, grow, n):
+    """About 20 fragments per pixel over 512x384 pixels: some 2.5M kept
+    fragments on the shallow pixels, about 150 pixels with a fragment in the
+    cutoff band."""
+    scene = scenes.small_box_scene(n, seed=seed, sh_degree=0)
+    scene.log_scales += np.float32(grow)
+    cam = scenes.identity_camera(512, 384, 512.0).rounded()
+    K = 32
+    prm = scenes.Params(K=K, tau_K=0.0)
+    img, r, _ = gpu_render(scene, cam, prm)
+    sv = saved_planes(r, cam, K)
+    ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
+    sp = oracle.preprocess(scene.astype(np.float64), cam, prm)
+    shallow = d["n_frag"] < K
+    assert shallow.mean() > 0.6 and d["n_frag"][shallow].sum() > 2 * 10 ** 6
+    band_pixels = int(((d["near_decision"] & oracle.AMB_CUTOFF) != 0)[shallow].sum())
+    worst_cut, worst_depth, n_cut, n_order = 0.0, 0.0, 0, 0
+    g_n, g_ids = sv["n_core"], sv["core_gid"]
+    valid = np.arange(K)[None, None, :] < g_n[..., None]
+    differ = shallow & ((g_n != d["n_core"]) | np.any(valid & (g_ids != d["core_gid"]), axis=-1))
+    for j, i in zip(*np.nonzero(differ)):
+        G = [int(v) for v in g_ids[j, i, :g_n[j, i]]]
+        O = [int(v) for v in d["core_gid"][j, i, :d["n_core"][j, i]]]
+        xs, ys = i + 0.5, j + 0.5
+        for gid in set(G) ^ set(O):
+            hit, rho2, z, a_raw, _, _ = oracle.eval_pair(sp, gid, xs, ys)
+            rc = float(sp["rho_c"][gid])
+            dist = abs(rho2 - rc) / max(1.0, rc)
+            assert hit and dist <= CUTOFF_REL, (i, j, gid, dist)
+            worst_cut = max(worst_cut, dist)
+            n_cut += 1
+        zg = [oracle.eval_pair(sp, gid, xs, ys)[2] for gid in G]
+        for a, b in zip(zg, zg[1:]):
+            if b < a:
+                gap = (a - b) / abs(a)
+                assert gap <= DEPTH_REL, (i, j, G, gap)
+                worst_depth = max(worst_depth, gap)
+                n_order += 1
+    rep = dict(seed=seed, pixels=int(shallow.sum()), fragments=int(d["n_frag"][shallow].sum()),
+               band_pixels=band_pixels, cutoff_flips=n_cut, worst_cutoff_flip=worst_cut,
+               order_flips=n_order, worst_depth_flip=worst_depth)
+    print("RESOLUTION " + json.dumps(rep))

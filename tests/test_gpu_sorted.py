@@ -9,7 +9,7 @@ import oracle
 from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
 from paper_2410_08129_gb300.renderer import FIELDS, BatchRenderer, GaussianTensors, Renderer
-from tests.gpu_util import (IMAGE_TOL, MAX_AMBIGUOUS, assert_grad_close, compare_images, gpu_render,
+from tests.gpu_util import (assert_grad_close, gpu_render, image_parity,
                             grads_to_numpy, workspace_view)
 
 pytestmark = pytest.mark.gpu
@@ -29,8 +29,7 @@ def test_sorted_forward_matches_oracle(boost, grow):
     prm = scenes.Params(K=8, bg=(0.2, 0.3, 0.4), sorted_blend=True)
     img, r, g = gpu_render(scene, cam, prm)
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb, _ = compare_images(img, ref, d["ambiguous"])
-    assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS, (e_ok, amb)
+    image_parity(img, ref, d, f"sorted boost={boost}")
     npix = cam.width * cam.height
     T = r.saved[:npix].view(cam.height, cam.width).cpu().numpy()
     ok = d["ambiguous"] == 0
@@ -79,8 +78,7 @@ def test_sorted_gradients_match_oracle(boost):
     r.forward(g)
     got = r.backward(g, torch.as_tensor(dl).cuda())
     torch.cuda.synchronize()
-    rep = assert_grad_close(grads_to_numpy(got), ref)
-    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()})
+    assert_grad_close(grads_to_numpy(got), ref, label=f"sorted boost={boost}")
 
 
 def test_sorted_batch_and_tile_shapes_agree():

@@ -12,8 +12,8 @@ import torch
 import oracle
 from paper_2410_08129_gb300 import binding as B
 from paper_2410_08129_gb300 import scenes
-from tests.gpu_util import (IMAGE_TOL, MAX_AMBIGUOUS, assert_core_ids, assert_grad_close, compare_images, gpu_render,
-                            grads_to_numpy, saved_planes, workspace_view)
+from tests.gpu_util import (assert_core_ids, assert_grad_close, gpu_render, grads_to_numpy, image_parity,
+                            saved_planes, workspace_view)
 
 pytestmark = pytest.mark.gpu
 
@@ -91,16 +91,15 @@ def test_items_cover_every_tile_list_once(dense):
 
 def test_split_image_parity(dense):
     scene, cam, prm, img, r, ref, d = dense
-    e_ok, amb, e_amb = compare_images(img, ref, d["ambiguous"])
-    print(f"split tiles: max err {e_ok:.3e}, ambiguous {amb:.4f} (max err {e_amb:.3e})")
-    assert np.isfinite(img).all()
-    assert e_ok <= IMAGE_TOL and amb <= MAX_AMBIGUOUS
+    # About 2000 fragments per pixel: the oracle marks 0.35% of the pixels
+    # ambiguous (cutoff and tau_K decisions, depth ties in the core).
+    image_parity(img, ref, d, "split tiles K=8", 0.0036)
 
 
 def test_split_core_ids(dense):
     scene, cam, prm, img, r, ref, d = dense
     sv = saved_planes(r, cam, prm.K)
-    assert assert_core_ids(sv, d) > 0.8
+    assert_core_ids(sv, d, scene, cam, prm, label="split tiles K=8")
 
 
 @pytest.mark.parametrize("K,tile,ppt", [(4, (16, 8), 2), (32, (16, 16), 1), (16, (8, 8), 2), (0, (16, 16), 4),
@@ -110,13 +109,14 @@ def test_split_launch_shapes(K, tile, ppt):
     prm = scenes.Params(K=K)
     img, r, _ = gpu_render(scene, cam, prm, tile=tile, ppt=ppt)
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    e_ok, amb, _ = compare_images(img, ref, d["ambiguous"])
-    # Thousands of candidates per pixel put the K-th and (K+1)-th depths of
-    # a large core within the oracle's tie margin on more pixels than usual.
-    assert e_ok <= IMAGE_TOL and amb <= (0.15 if K >= 32 else MAX_AMBIGUOUS), (e_ok, amb)
+    # Thousands of fragments per pixel put cutoff decisions and adjacent
+    # depths of a large core within the oracle's margins on many pixels: it
+    # marks 0.66, 0.99, 0.46, 1.00 and 0.44% ambiguous at K = 4, 32, 16, 0, 8.
+    cap = {4: 0.0067, 32: 0.0099, 16: 0.0046, 0: 0.0101, 8: 0.0045}[K]
+    image_parity(img, ref, d, f"split shapes K={K} {tile} ppt={ppt}", cap)
     if K:
         sv = saved_planes(r, cam, K)
-        assert assert_core_ids(sv, d) > 0.5
+        assert_core_ids(sv, d, scene, cam, prm, label=f"split shapes K={K}")
 
 
 def test_split_deterministic(dense):
@@ -140,5 +140,4 @@ def test_split_gradients():
     assert n_items > lay.n_tiles, "the scene must split some tiles"
     grads = r.backward(g, torch.as_tensor(dl).cuda())
     torch.cuda.synchronize()
-    rep = assert_grad_close(grads_to_numpy(grads), ref)
-    print({k: f"{v[0]:.2e}/{v[1]:.2f}" for k, v in rep.items()})
+    assert_grad_close(grads_to_numpy(grads), ref, label="split tiles K=8")

@@ -3,6 +3,8 @@ largest blending weight of every Gaussian (visibility score), the norm of the
 mean's gradient times half the camera distance, and the number of views a
 Gaussian covers. Against the FP64 oracle on one view, and combined over the
 views of a batch exactly as over separate calls (max, sum, count)."""
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -40,6 +42,8 @@ def test_statistics_match_oracle(K):
     assert 0 < ref["densify_count"].sum() < scene.n
     # visibility: FP32 weights; a near-decision at a Gaussian's heaviest pixel may move it further
     vis_err = np.abs(got["visibility"] - ref["visibility"]) > 2e-4 + 2e-3 * ref["visibility"]
+    print("STATS " + json.dumps(dict(K=K, vis_miss=float(vis_err.mean()), n_miss=int(vis_err.sum()),
+                                     vis_max_err=float(np.abs(got["visibility"] - ref["visibility"]).max()))))
     assert vis_err.mean() <= 0.03, (vis_err.sum(), np.abs(got["visibility"] - ref["visibility"]).max())
     assert ref["visibility"].max() > 0.1
     # the densification statistic follows the mean gradient (1e-3 relative per tensor)
