@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p frames/s @1M Gaussians and fwd+bwd steps/s, batched vs plain, at oracle tol"
 UNIT = "frames/s"
 WORKLOAD = "1M clustered Gaussians, SH deg 3, 1920x1080, 60deg vFOV, K=8, tau_alpha=1/255, tau_K=0.05"
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES = 128  # FP32 lanes per SM (sm_100 family)
 
 
 def _peaks():
@@ -157,20 +157,83 @@ def _dist():
     return world, rank, local
 
 
-def cpu_baseline(scene, cam, prm, window=(944, 524, 32, 32)):
-    """The FP64 oracle (as it stands) on a bounded window of the same frame,
-    extrapolated to frames/s."""
+def _lscpu():
+    """Host CPU description from lscpu (model, logical CPUs)."""
+    out = {"os_cpu_count": os.cpu_count()}
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return out
+    for ln in txt.splitlines():
+        k, _, v = ln.partition(":")
+        if k.strip() in ("CPU(s)", "Model name", "Architecture", "Thread(s) per core", "Core(s) per socket"):
+            out[k.strip()] = v.strip()
+    return out
+
+
+def _oracle_window(scene64, cam, prm, window):
     import oracle
-    s64 = scene.astype(np.float64)
     t0 = time.perf_counter()
-    oracle.render(s64, cam, prm, window=window)
-    dt = time.perf_counter() - t0
-    w, h = window[2], window[3]
-    fps = 1.0 / (dt * cam.width * cam.height / (w * h))
+    oracle.render(scene64, cam, prm, window=window)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(scene, cam, prm, stress_scene, stress_cam):
+    """The FP64 oracle as it stands (brute force: every Gaussian against every
+    pixel) on the host cores, on the samples the measurement plan names: the
+    64x64 frame of 256 Gaussians in full, a 128x128 crop of the headline 1080p
+    frame and a 128x128 crop of the 6M-Gaussian stress frame (16 of its 128
+    rows, the rest extrapolated). value = headline frames/s extrapolated from
+    the crop's time per pixel."""
+    import oracle
+    from paper_2410_08129_gb300 import scenes
+    runs = []
+    s1, c1, p1, _ = scenes.config1()
+    dt = _oracle_window(s1.astype(np.float64), c1.rounded(), p1, None)
+    runs.append({"sample": "256 Gaussians, 64x64, full frame", "s": dt, "pairs": s1.n * 64 * 64,
+                 "pairs_per_s": s1.n * 64 * 64 / dt})
+    cx, cy = cam.width // 2 - 64, cam.height // 2 - 64
+    dt2 = _oracle_window(scene.astype(np.float64), cam, prm, (cx, cy, 128, 128))
+    runs.append({"sample": f"{scene.n} Gaussians, 128x128 crop at ({cx},{cy}) of 1920x1080", "s": dt2,
+                 "pairs": scene.n * 128 * 128, "pairs_per_s": scene.n * 128 * 128 / dt2})
+    sx, sy = stress_cam.width // 2 - 64, stress_cam.height // 2 - 64
+    dt5 = _oracle_window(stress_scene.astype(np.float64), stress_cam, prm, (sx, sy, 128, 16))
+    runs.append({"sample": f"{stress_scene.n} Gaussians, rows 0-15 of the 128x128 crop at ({sx},{sy}) of "
+                           f"the stress frame; crop time extrapolated", "s": dt5, "crop_s_extrapolated": 8 * dt5,
+                 "pairs": stress_scene.n * 128 * 16, "pairs_per_s": stress_scene.n * 128 * 16 / dt5})
+    fps = 1.0 / (dt2 * cam.width * cam.height / (128 * 128))
     return {"value": fps, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{w}x{h} window at ({window[0]},{window[1]}) of the 1080p frame, all {scene.n} "
-                      f"Gaussians brute-forced per pixel; {dt:.2f} s, extrapolated to the full frame",
-            "pairs_per_s": scene.n * w * h / dt}
+            "sample": "headline frames/s extrapolated from a 128x128 crop of the 1080p frame "
+                      f"({dt2:.1f} s, all Gaussians brute-forced per pixel)",
+            "runs": runs, "lscpu": _lscpu()}
+
+
+def fp32_peak(local):
+    """FP32 FMA rate of this device: SM count from the device properties and
+    the rate measured by the FMA-chain probe (best of 5 launches of about
+    5 ms, CUDA events), with the SM clock sampled during the probe."""
+    import torch
+    from paper_2410_08129_gb300 import binding as B
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    blocks, iters = sms * 8, 5000
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    B.htgs_fma_probe(blocks, iters, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    with ClockSampler(local) as ck:
+        for _ in range(5):
+            e0.record()
+            n = B.htgs_fma_probe(blocks, iters, out)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    rate = n / (best / 1e3)
+    clk = ck.summary()
+    mhz = clk["sm_mhz"] or clk["sm_max_mhz"]
+    nominal = sms * FP32_LANES * mhz * 1e6 if mhz else None
+    return {"sms": sms, "fma_per_s": rate, "probe_ms": best, "sm_mhz": mhz, "clocks": clk,
+            "nominal_at_clock": nominal, "frac_of_nominal": rate / nominal if nominal else None}
 
 
 def run_reference(args):
@@ -849,61 +912,77 @@ def main():
     sorted_train_ms = max_over_ranks(u0.elapsed_time(u1)) / max(3, n_train // 2)
     del str_, starget
 
-    # ---- roofline of the dominant kernel (the forward blend) ---------------
-    # Algorithmic FP32-pipe instructions of the quadratic-form evaluation:
-    # 8 per pixel inside a tight bounding box (2 offsets, 5 FMA, 1 compare),
-    # 14 per kept fragment (denominator 5 FMA, 2 mul, 1 min, 5 tail sums,
-    # 1 count), 10 per core candidate (depth 6, key and compare 4) and 8K per
-    # core insertion; the peak is 152 SMs x 128 FP32 lanes x 2070 MHz.
+    # ---- roofline of every kernel group, in the work units of the plan -----
+    # FP32-bound blends: algorithmic FP32 lane-instructions of the direct
+    # (Pluecker) evaluation per the measurement plan: 27 per (pixel, Gaussian)
+    # pair tested (8 FMA for the planes a, b; 6 for d; 6 for m; 6 for the two
+    # norms; 1 compare), +20 per kept fragment (alpha, depth, blending); the
+    # adjoint re-tests every pair (27) and spends 2.5x the forward's 20 per
+    # kept fragment (50; the plan gives 2-3x). P = pixels inside the
+    # Gaussians' tight boxes, A = kept fragments (htgs_get_counters). Peak =
+    # the FMA probe's measured rate, scaled by the ratio of the SM clock
+    # sampled during the timed region to the one during the probe.
+    # The implementation's own instruction counts (its quadratic-form
+    # evaluation needs fewer per pair) are kept as `impl_work`.
+    # HBM-bound phases: algorithmic bytes per the plan (preprocess: the
+    # parameters in, an 84-byte record, an 8-byte tile rectangle and a 4-byte
+    # count out per Gaussian; binning and sort: 32 B per instance) over the
+    # phase's CUDA-event time, against the measured copy bandwidth.
     K = prm.K
+    fp32 = fp32_peak(local)
+    probe_mhz = fp32["sm_mhz"]
 
-    def fwd_work(c, k):
+    def fp32_peak_at(clk):
+        mhz = clk.get("sm_mhz") or probe_mhz
+        return fp32["fma_per_s"] * (mhz / probe_mhz if probe_mhz else 1.0)
+
+    def plan_fwd(c):
+        return 27 * c["box_pairs"] + 20 * c["kept"]
+
+    def impl_fwd(c, k):
         return 8 * c["box_pairs"] + 14 * c["kept"] + 10 * c["admitted"] + 8 * k * c["inserted"]
 
-    alg = fwd_work(counters, K)
+    head_clocks = clocks.summary()
+    peak = fp32_peak_at(head_clocks)
+    alg = plan_fwd(counters)
     blend_s = float(np.mean(blend_ms)) / 1e3
-    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6
     achieved = alg / blend_s
     traffic = recorded_traffic()
-
-    # ---- every kernel group against its own roofline ------------------------
-    # HBM-bound phases: algorithmic bytes (each byte the phase must move once)
-    # over the phase's CUDA-event time, against the measured copy bandwidth.
-    # Preprocess: parameters in (3 + 3 + 4 + 1 + 3 (deg + 1)^2 floats), the
-    # 128-byte record, the 8-byte tile rectangle and the 4-byte count out.
-    # Binning and sort: the count read and an 8-byte (key, value) write per
-    # instance (emit), a 4-byte key read (histogram), a 16-byte read and write
-    # per digit pass, a 4-byte key read (ranges).
-    # ALU-bound blends: algorithmic FP32-pipe instructions (forward as above;
-    # adjoint 8 per pixel inside a box and 28 per kept fragment: alpha 5,
-    # 1 / (1 - alpha) 2, dL/dalpha 5, colour sums 3, g, e, e t 5, the six
-    # packed moment updates and their two products 8) against the FP32 peak.
     hbm_peak = float(peaks["hbm_gbs"]) * 1e9
     nc = (scene.sh_degree + 1) ** 2
-    pre_bytes = scene.n * ((3 + 3 + 4 + 1 + 3 * nc) * 4 + 128 + 8 + 4)
+    pre_unit = (3 + 3 + 4 + 1 + 3 * nc) * 4 + 84 + 8 + 4
+    pre_bytes = scene.n * pre_unit
     n_tiles = -(-cam.width // fwd_shape[0][0]) * -(-cam.height // fwd_shape[0][1])
     passes = -(-max(1, int(n_tiles - 1).bit_length()) // 9)
-    bin_bytes = scene.n * 4 + inst * (8 + 4 + 32 * passes + 4)
+    bin_bytes = 32 * inst
     pre_s, bin_s = float(np.mean(pre_ms)) / 1e3, float(np.mean(bin_ms)) / 1e3
     tfwd_s, tbwd_s = float(np.mean(fwd_blend_train_ms)) / 1e3, float(np.mean(bwd_blend_ms)) / 1e3
-    bwd_alg = 8 * tcounters["box_pairs"] + 28 * tcounters["kept"]
+    train_peak = fp32_peak_at(train_clocks.summary())
 
-    def line(bound, work, secs, pk, unit, scale, per_unit):
-        return {"bound": bound, "achieved": work / secs / scale, "peak": pk / scale, "unit": unit,
-                "frac": work / secs / pk, "ms": secs * 1e3, "work": work, "work_per_unit": per_unit}
+    def line(bound, work, secs, pk, unit, scale, per_unit, **extra):
+        return dict({"bound": bound, "achieved": work / secs / scale, "peak": pk / scale, "unit": unit,
+                     "frac": work / secs / pk, "ms": secs * 1e3, "work": work, "work_per_unit": per_unit},
+                    **extra)
 
+    fwd_units = "27 FP32 instr per box pair + 20 per kept fragment"
     kernels = {
         "preprocess_1080p": line("hbm", pre_bytes, pre_s, hbm_peak, "GB/s", 1e9,
-                                 f"{pre_bytes // scene.n} B per Gaussian"),
-        "binning_sort_1080p": line("hbm", bin_bytes, bin_s, hbm_peak, "GB/s", 1e9,
-                                   f"4 B per Gaussian + {8 + 4 + 32 * passes + 4} B per instance ({passes} passes)"),
-        "blend_fwd_1080p": line("alu", alg, blend_s, peak, "T FP32 instr/s", 1e12,
-                                "8/box pair + 14/kept + 10/candidate + 8K/insertion"),
-        "blend_fwd_train": line("alu", fwd_work(tcounters, tprm.K), tfwd_s, peak, "T FP32 instr/s", 1e12,
-                                "8/box pair + 14/kept + 10/candidate + 8K/insertion"),
-        "blend_bwd_train": line("alu", bwd_alg, tbwd_s, peak, "T FP32 instr/s", 1e12,
-                                "8/box pair + 28/kept"),
+                                 f"{pre_unit} B per Gaussian ({pre_unit - 96} in, 96 out)"),
+        "binning_sort_1080p": line("hbm", bin_bytes, bin_s, hbm_peak, "GB/s", 1e9, "32 B per instance",
+                                   instances=inst),
+        "blend_fwd_1080p": line("alu", alg, blend_s, peak, "T FP32 instr/s", 1e12, fwd_units,
+                                impl_work=impl_fwd(counters, K),
+                                impl_frac=impl_fwd(counters, K) / blend_s / peak),
+        "blend_fwd_train": line("alu", plan_fwd(tcounters), tfwd_s, train_peak, "T FP32 instr/s", 1e12,
+                                fwd_units, impl_work=impl_fwd(tcounters, tprm.K),
+                                impl_frac=impl_fwd(tcounters, tprm.K) / tfwd_s / train_peak),
+        "blend_bwd_train": line("alu", 27 * tcounters["box_pairs"] + 50 * tcounters["kept"], tbwd_s, train_peak,
+                                "T FP32 instr/s", 1e12, "27 FP32 instr per box pair + 50 per kept fragment",
+                                impl_work=8 * tcounters["box_pairs"] + 28 * tcounters["kept"],
+                                impl_frac=(8 * tcounters["box_pairs"] + 28 * tcounters["kept"]) / tbwd_s
+                                / train_peak),
         "hbm_peak_source": f"hbm_gbs, {peak_src}",
+        "fp32_peak": fp32,
     }
 
     # ---- stress: 6M Gaussians with flat, near-plane and opaque splats --------
@@ -936,7 +1015,7 @@ def main():
         stress[str(kk)] = {"value": job_throughput(1, world, sms), "unit": "steps/s", "ms_per_step": sms,
                            "instances": sinst, "finite": finite}
         del srr, simg, sdl, sgrads
-    del sgs, sscene
+    del sgs
     torch.cuda.empty_cache()
 
     batched = None
@@ -948,7 +1027,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(scene, cam, prm)
+        cpu = cpu_baseline(scene, cam, prm, sscene, scam)
+    del sscene
 
     line = {
         "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -989,12 +1069,15 @@ def main():
                 "overlap": "uploads and read-backs on two copy streams, double-buffered, overlapping the renders"},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (no FP32 figure in MEASURED_PEAKS.json)"},
+                     "work": f"{fwd_units}: {alg:.4g} per launch",
+                     "peak_source": f"FMA-chain probe, measured {fp32['fma_per_s'] / 1e12:.2f} T/s at "
+                                    f"{probe_mhz} MHz on {fp32['sms']} SMs (device properties), scaled to the "
+                                    f"{head_clocks.get('sm_mhz')} MHz sampled during the timed region"},
         "kernels": kernels,
         # per frame: preprocess, scan, emit, histogram, the digit passes,
         # ranges, schedule and the blend
         "gpu_launches": args.steps * (7 + passes),
-        "clocks": clocks.summary(),
+        "clocks": head_clocks,
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -150,7 +150,15 @@ typedef struct {
                                     digit pass the first block also waits for a look-back word that
                                     nothing writes; the bounded wait gives up, the sort completes
                                     correctly, the blend is skipped and htgs_get_error reports
-                                    HTGS_ERR_TIMEOUT */
+                                    HTGS_ERR_TIMEOUT (forces the radix-sort binning) */
+    int32_t binning;          /* how tile lists are built; every choice gives the same lists (the
+                                 records covering each tile in record order, or in mean-depth
+                                 order for sorted blending): 0 (default) a stable counting sort by
+                                 tile when every tile's counters fit shared memory (at most 16384
+                                 tiles over all views) and its per-(2048 records, tile) count
+                                 matrix is at most 4x the instance capacity, else the radix sort;
+                                 1 the stable LSD radix sort of tile keys; 2 the counting sort
+                                 (HTGS_ERR_NOT_SUPPORTED where it does not fit) */
 } htgs_launch;
 
 /* Sizes of the caller-owned buffers for one camera.
@@ -339,6 +347,18 @@ htgs_status htgs_render_static(const htgs_gaussians *gaussians, const htgs_camer
  * Asynchronous on `stream`. HTGS_ERR_INVALID_ARG for a NULL or misaligned
  * buffer or invalid parameters. */
 htgs_status htgs_bake(const htgs_gaussians *gaussians, float *baked, void *stream);
+
+/* FP32-pipe throughput probe (a measurement aid; the paper has no
+ * counterpart). Launches `blocks` CTAs of 256 threads; each thread runs 8
+ * independent chains of 16 * iters fused multiply-adds, then writes one
+ * float to out (blocks * 256 floats, device, caller-owned). Timing the launch
+ * with events on `stream` gives the device's FP32 FMA rate, the roofline of
+ * the blend kernels (which use no tensor cores).
+ *   fma_per_launch  [out] host: FMA instructions per thread-lane summed
+ *                   over the launch, blocks * 256 * iters * 128
+ * Asynchronous on `stream`. HTGS_ERR_INVALID_ARG for a non-positive size or
+ * a NULL pointer; HTGS_ERR_CUDA when the launch fails. */
+htgs_status htgs_fma_probe(int32_t blocks, int32_t iters, float *out, void *stream, int64_t *fma_per_launch);
 
 /* Static string for a status code. */
 const char *htgs_status_string(htgs_status status);

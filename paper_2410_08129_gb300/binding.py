@@ -63,7 +63,7 @@ class Launch(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("px_per_thread", ctypes.c_int32), ("depth_bits", ctypes.c_int32),
                 ("smem_batch", ctypes.c_int32), ("events", ctypes.c_void_p * 6),
-                ("test_lookback_stall", ctypes.c_int32)]
+                ("test_lookback_stall", ctypes.c_int32), ("binning", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -113,6 +113,9 @@ def lib():
                                              ctypes.c_void_p]
             L.htgs_render_static.restype = ctypes.c_int32
             L.htgs_bake.argtypes = [P(Gaussians), ctypes.c_void_p, ctypes.c_void_p]
+            L.htgs_fma_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         P(ctypes.c_int64)]
+            L.htgs_fma_probe.restype = ctypes.c_int32
             L.htgs_bake.restype = ctypes.c_int32
             L.htgs_status_string.argtypes = [ctypes.c_int32]
             L.htgs_status_string.restype = ctypes.c_char_p
@@ -156,12 +159,16 @@ def c_params(p) -> Params:
     return q
 
 
+BINNING_AUTO, BINNING_RADIX, BINNING_COUNTING = 0, 1, 2
+
+
 def c_launch(tile=(16, 16), px_per_thread=0, depth_bits=0, events=None, smem_batch=0,
-             test_lookback_stall=0) -> Launch:
+             test_lookback_stall=0, binning=BINNING_AUTO) -> Launch:
     """events: up to 6 torch.cuda.Event(enable_timing=True) (or None) recorded
     around the render phases, see htgs_launch in include/htgs.h."""
     L = Launch(int(tile[0]), int(tile[1]), int(px_per_thread), int(depth_bits), int(smem_batch))
     L.test_lookback_stall = int(test_lookback_stall)
+    L.binning = int(binning)
     for i, e in enumerate(events or []):
         L.events[i] = e.cuda_event if e is not None else None
     return L
@@ -254,6 +261,14 @@ def htgs_get_counters(workspace, stream=None):
                                  _stream(stream), out)
     _check(st, "htgs_get_counters")
     return dict(box_pairs=int(out[0]), kept=int(out[1]), admitted=int(out[2]), inserted=int(out[3]))
+
+
+def htgs_fma_probe(blocks, iters, out, stream=None):
+    """Launches the FP32 FMA-chain probe; returns the FMAs per launch."""
+    n = ctypes.c_int64(0)
+    _check(lib().htgs_fma_probe(int(blocks), int(iters), _ptr(out), _stream(stream), ctypes.byref(n)),
+           "htgs_fma_probe")
+    return int(n.value)
 
 
 def htgs_l1_loss_grad(image, target, dl_dimage, loss, stream=None):
