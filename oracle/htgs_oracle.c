@@ -117,7 +117,7 @@ typedef struct {
    more than OG_EFFECT_TOL (found by blending the pixel again with the
    decision flipped). */
 enum {
-    OG_AMB_CUTOFF = 1,   /* |rho^2 - rho_c| <= 2e-5 max(1, rho_c) */
+    OG_AMB_CUTOFF = 1,   /* |rho^2 - rho_c| <= 4e-6 max(1, rho_c) */
     OG_AMB_TAUK = 2,     /* |alpha - tau_K| <= 2e-6 */
     OG_AMB_AMAX = 4,     /* |o e^{-rho^2/2} - alpha_max| <= 1e-6 */
     OG_AMB_CORE_EDGE = 8,/* K-th and (K+1)-th candidate depths within 1e-6 |z| */
@@ -128,7 +128,7 @@ enum {
 };
 /* Sorted blending stops before the fragment that would take T below this. */
 #define OG_SORTED_TMIN 1e-4
-#define OG_CUTOFF_REL 2e-5
+#define OG_CUTOFF_REL 4e-6
 #define OG_TAUK_ABS 2e-6
 #define OG_AMAX_ABS 1e-6
 #define OG_DEPTH_REL 1e-6

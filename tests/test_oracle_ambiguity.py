@@ -28,7 +28,7 @@ TAU_A = 1.0 / 255.0
 W = H = 16
 FX = 16.0
 CX = CY = 8.5   # the ray through pixel (8, 8) is the optical axis
-CUT_REL, TAUK_ABS, AMAX_ABS, DEPTH_REL, EFFECT = 2e-5, 2e-6, 1e-6, 1e-6, 2e-5
+CUT_REL, TAUK_ABS, AMAX_ABS, DEPTH_REL, EFFECT = 4e-6, 2e-6, 1e-6, 1e-6, 2e-5
 Y00 = 0.5 / math.sqrt(math.pi)
 
 
@@ -96,14 +96,14 @@ def _flagged(mask):
 
 @pytest.mark.parametrize("side", [+1, -1])
 def test_cutoff_band_flags_exactly_the_band(side):
-    """rho_c placed 1e-5 (relative) above or below rho^2 at pixel (10, 8):
+    """rho_c placed 2e-6 (relative) above or below rho^2 at pixel (10, 8):
     the four symmetric pixels carry the cutoff bit and no other pixel does;
     the fragment there has alpha ~ tau_alpha, so keeping or dropping it
     moves the colour by alpha * c (> 2e-5): ambiguous, with that move as the
     pixel's budget. A kept fragment is counted, a rejected one is not."""
     centre, sigma, rgb = (0.0, 0.0, 3.0), 0.3, (1.0, 0.5, 0.2)
     r2p, _ = _rho2_z(centre, sigma, 10, 8)
-    rho_c = r2p * (1 + side * 1e-5)
+    rho_c = r2p * (1 + side * 2e-6)
     o = _opacity_for_cutoff(rho_c)
     band, edge = _band_pixels(centre, sigma, rho_c)
     assert edge > 0.2
@@ -121,10 +121,10 @@ def test_cutoff_band_flags_exactly_the_band(side):
     assert np.all(d["amb_effect"][d["near_decision"] == 0] == 0.0)
 
 
-@pytest.mark.parametrize("rel", [5e-5, -5e-5, 1e-4])
+@pytest.mark.parametrize("rel", [1e-5, -1e-5, 1e-4])
 def test_cutoff_just_outside_the_band_is_not_flagged(rel):
-    """rho_c 5e-5 or 1e-4 (relative) away from rho^2 at pixel (10, 8): the
-    band (2e-5) does not reach it and no pixel is flagged."""
+    """rho_c 1e-5 or 1e-4 (relative) away from rho^2 at pixel (10, 8): the
+    band (4e-6) does not reach it and no pixel is flagged."""
     centre, sigma = (0.0, 0.0, 3.0), 0.3
     r2p, _ = _rho2_z(centre, sigma, 10, 8)
     rho_c = r2p * (1 + rel)
@@ -140,7 +140,7 @@ def test_cutoff_band_without_colour_move_is_not_ambiguous():
     decision is near (flagged) but neither side moves the colour."""
     centre, sigma, rgb = (0.0, 0.0, 3.0), 0.3, (0.25, 0.5, 0.75)
     r2p, _ = _rho2_z(centre, sigma, 10, 8)
-    o = _opacity_for_cutoff(r2p * (1 + 1e-5))
+    o = _opacity_for_cutoff(r2p * (1 + 2e-6))
     img, d, _ = _render([(centre, sigma, o, rgb)], bg=rgb)
     assert _flagged(d["near_decision"] != 0) == {(10, 8), (6, 8), (8, 10), (8, 6)}
     assert not d["ambiguous"].any()

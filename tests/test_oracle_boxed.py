@@ -47,8 +47,8 @@ def test_boxed_equals_brute_force_on_the_stress_distribution(stress, win, K):
 def test_boxed_keeps_the_cutoff_band():
     """A dense scene with a few dozen pixels in the cutoff band: the boxed
     render flags the same ones."""
-    scene = scenes.small_box_scene(3000, seed=13, sh_degree=1).astype(np.float64)
-    scene.log_scales += 0.8
+    scene = scenes.small_box_scene(20000, seed=13, sh_degree=1).astype(np.float64)
+    scene.log_scales += 0.6
     cam = scenes.identity_camera(64, 48, 60.0)
     d, _ = _check(scene, cam, scenes.Params(K=4), (8, 8, 40, 32), subset=False)
     assert (d["near_decision"] & oracle.AMB_CUTOFF != 0).sum() >= 20
@@ -56,7 +56,7 @@ def test_boxed_keeps_the_cutoff_band():
 
 
 def test_boxed_sees_a_band_pixel_outside_the_rectangle():
-    """An isotropic splat whose cutoff lies 1e-5 (relative) inside rho^2 at
+    """An isotropic splat whose cutoff lies 2e-6 (relative) inside rho^2 at
     pixel (40, 24): that pixel is rejected, so it lies outside the splat's
     covered rectangle, yet it is a near-decision. A window holding that
     pixel but none of the rectangle must still flag it. (Row 24's centre is
@@ -67,7 +67,7 @@ def test_boxed_sees_a_band_pixel_outside_the_rectangle():
     r = np.array([(40.5 - cam.cx) / cam.fx, (24.5 - cam.cy) / cam.fy, 1.0])
     r /= np.linalg.norm(r)
     rho2 = (c @ c - (c @ r) ** 2) / sigma ** 2
-    o = (1 / 255) * np.exp(0.5 * rho2 * (1 - 1e-5))
+    o = (1 / 255) * np.exp(0.5 * rho2 * (1 - 2e-6))
     scene = scenes.Scene(c[None], np.full((1, 3), np.log(sigma)), np.array([[1.0, 0, 0, 0]]),
                          np.array([np.log(o / (1 - o))]), np.full((1, 1, 3), 1.0), 0)
     sp = oracle.preprocess(scene, cam, scenes.Params(K=4))
