@@ -478,7 +478,7 @@ def batched_leg(steps, warmup):
     return out
 
 
-def profile_case(which: str, warmup: int, tile=None, ppt: int = 1):
+def profile_case(which: str, warmup: int, tile=None, ppt: int = 1, binning: int = 0):
     """A few untimed steps of the headline render (fwd) or of the training
     step (train): `warmup` steps, then 2 more, nothing else on the GPU. The
     launch shape defaults to the one the autotuner picks for the workload on
@@ -491,7 +491,7 @@ def profile_case(which: str, warmup: int, tile=None, ppt: int = 1):
     if which == "fwd":
         scene, cam, prm = scenes.config2()
         g = GaussianTensors.from_scene(scene)
-        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (16, 16), ppt))
+        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (16, 16), ppt, binning=binning))
         img = r.image_buffer()
         r.forward(g, image=img, save=False, check=True)
         for _ in range(warmup + 2):
@@ -499,7 +499,7 @@ def profile_case(which: str, warmup: int, tile=None, ppt: int = 1):
     else:
         scene, target, cam, prm = scenes.config3()
         g = GaussianTensors.from_scene(scene)
-        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (32, 16), ppt))
+        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (32, 16), ppt, binning=binning))
         img = r.image_buffer()
         tgt = r.forward(GaussianTensors.from_scene(target), save=False, check=True).clone()
         dl = torch.empty_like(img)
@@ -529,13 +529,16 @@ def main():
                     help="run a few untimed steps of one workload (for an external profiler) and exit")
     ap.add_argument("--profile-tile", default=None, help="tile shape WxH of --profile (default: the autotuner's pick)")
     ap.add_argument("--profile-ppt", type=int, default=1, help="forward pixels per thread of --profile")
+    ap.add_argument("--profile-binning", choices=["radix", "counting"], default="radix",
+                    help="tile binning of --profile (the lists are the same)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile:
         tile = tuple(int(v) for v in args.profile_tile.split("x")) if args.profile_tile else None
-        profile_case(args.profile, args.warmup, tile, args.profile_ppt)
+        profile_case(args.profile, args.warmup, tile, args.profile_ppt,
+                     binning=2 if args.profile_binning == "counting" else 1)
         return
 
     import torch

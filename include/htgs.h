@@ -151,14 +151,12 @@ typedef struct {
                                     nothing writes; the bounded wait gives up, the sort completes
                                     correctly, the blend is skipped and htgs_get_error reports
                                     HTGS_ERR_TIMEOUT (forces the radix-sort binning) */
-    int32_t binning;          /* how tile lists are built; every choice gives the same lists (the
-                                 records covering each tile in record order, or in mean-depth
-                                 order for sorted blending): 0 (default) a stable counting sort by
-                                 tile when every tile's counters fit shared memory (at most 16384
-                                 tiles over all views) and its per-(2048 records, tile) count
-                                 matrix is at most 4x the instance capacity, else the radix sort;
-                                 1 the stable LSD radix sort of tile keys; 2 the counting sort
-                                 (HTGS_ERR_NOT_SUPPORTED where it does not fit) */
+    int32_t binning;          /* how tile lists are built; both give the same lists (the records
+                                 covering each tile in record order, or in mean-depth order for
+                                 sorted blending): 0 (default) or 1 the stable LSD radix sort of
+                                 tile keys; 2 a stable counting sort by tile computed from the
+                                 records' tile rectangles, for a single view whose tile rows are
+                                 at most 2048 tiles long (HTGS_ERR_NOT_SUPPORTED otherwise) */
 } htgs_launch;
 
 /* Sizes of the caller-owned buffers for one camera.
@@ -323,14 +321,22 @@ htgs_status htgs_l1_loss_grad(const float *image, const float *target, int64_t n
  * allocation (which may synchronise the device) is not allowed. The paper
  * has no counterpart of this entry point.
  *   image   [out] height x width x 3 float32, device (caller-owned)
+ * Size limit: the workspace of htgs_workspace_size must fit the array. That
+ * is about 208 bytes per Gaussian (the blend record, tile rectangle and
+ * count, and the per-Gaussian accumulators the layout keeps) plus a small
+ * per-tile part, so at most about 161,000 Gaussians even with no tile
+ * instances; the rest of the array holds the instances, at about
+ * 18 + (6 + 2K) * tile_pixels / 128 bytes each (44 at K = 4 with 16x16
+ * tiles). Beyond the first limit the call returns HTGS_ERR_WORKSPACE, beyond
+ * the second HTGS_ERR_OVERFLOW.
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
- * capture. The call synchronises `stream` before returning and returns
- * HTGS_ERR_WORKSPACE when the scene needs more scratch than the array holds
- * (too many Gaussians for 32 MiB) and HTGS_ERR_OVERFLOW when its tile
- * instances do not fit the rest of it. Every call shares the one array and
- * the render clears what must start at zero; calls that overlap on the GPU
- * (two streams, or two host threads on one device) race on it. */
+ * capture. A device reset (cudaDeviceReset) reloads the library's device
+ * code, so the cached address must not be used after one: call this entry
+ * point only in processes that do not reset the device. The call
+ * synchronises `stream` before returning. Every call shares the one array
+ * and the render clears what must start at zero; calls that overlap on the
+ * GPU (two streams, or two host threads on one device) race on it. */
 htgs_status htgs_render_static(const htgs_gaussians *gaussians, const htgs_camera *cam,
                                const htgs_params *params, const htgs_launch *launch, float *image,
                                void *stream);

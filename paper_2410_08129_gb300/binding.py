@@ -26,6 +26,7 @@ HTGS_ERR_TIMEOUT = 5
 HTGS_ERR_NOT_SUPPORTED = 6
 HTGS_MAX_K = 32
 HTGS_MAX_CAPACITY = (1 << 31) - 1
+HTGS_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class Gaussians(ctypes.Structure):

@@ -389,7 +389,53 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a)
     __shared__ uint32_t s_cnt[kSchedBuckets];
     __shared__ uint32_t s_pos[kSchedBuckets];
     __shared__ uint32_t s_slots;
+    __shared__ unsigned long long s_wt[kSchedThreads / 32];
     const int tid = threadIdx.x;
+    if (a.tile_tot) {
+        // Counting-sort binning: tile ranges and the instance total from the
+        // per-tile counts. Thread tid owns tiles [tid * per, tid * per + per).
+        const int T = a.n_tiles, lane = tid & 31, warp = tid >> 5;
+        const int per = (T + kSchedThreads - 1) / kSchedThreads;
+        const int t0 = tid * per;
+        unsigned long long loc = 0;
+        for (int k = 0; k < per; ++k)
+            if (t0 + k < T) loc += a.tile_tot[t0 + k];
+        unsigned long long incl = loc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) s_wt[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long v = s_wt[lane];
+            unsigned long long vi = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long x = __shfl_up_sync(kFull, vi, o);
+                if (lane >= o) vi += x;
+            }
+            s_wt[lane] = vi - v;
+        }
+        __syncthreads();
+        unsigned long long run = s_wt[warp] + incl - loc;
+        for (int k = 0; k < per; ++k)
+            if (t0 + k < T) {
+                const uint32_t c = a.tile_tot[t0 + k];
+                a.ranges_out[t0 + k] = make_uint2((uint32_t)run, (uint32_t)(run + c));
+                run += c;
+            }
+        if (tid == kSchedThreads - 1) {
+            a.status[kStInstLo] = (int)(uint32_t)(run & 0xffffffffull);
+            a.status[kStInstHi] = (int)(uint32_t)(run >> 32);
+            if (run > (unsigned long long)a.capacity) {
+                set_error(a.status, HTGS_ERR_OVERFLOW);
+                *a.total_out = 0;
+            } else {
+                *a.total_out = (uint32_t)run;
+            }
+        }
+        __syncthreads();
+    }
     // After a recorded failure the tile ranges may not describe the list
     // (keys a bounded wait left unsorted): schedule nothing.
     if (a.status[kStError] != 0) {

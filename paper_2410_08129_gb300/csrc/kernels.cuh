@@ -143,7 +143,43 @@ struct ScheduleArgs {
     int slots_cap;         // partial-state slots available
     int4 *items;           // n_tiles + slots_cap
     uint32_t *n_items;
-    const int *status;     // a recorded failure (overflow, a wait that gave up): no items
+    int *status;           // a recorded failure (overflow, a wait that gave up): no items
+    // Counting-sort binning: the per-tile instance counts. When set, the
+    // kernel first writes ranges_out (exclusive scan of the counts) and
+    // total_out (the instance total, 0 on overflow), checks the capacity and
+    // records the total in the status slots.
+    const uint32_t *tile_tot;
+    uint2 *ranges_out;
+    uint32_t *total_out;
+    int64_t capacity;
+};
+
+// Counting-sort binning of a single view (tilesort.cu): blocks of `gauss`
+// emission positions (kCsMinGauss .. kCsMaxGauss, so that per-block tile
+// counts fit 16 bits), bands of whole tile rows of at most kCsBandTiles tiles.
+constexpr int kCsWarps = 8;
+constexpr int kCsThreads = 32 * kCsWarps;
+constexpr int kCsBandTiles = 2048;   // shared memory: 5 x 4 B per band tile in cs_emit
+constexpr int kCsMinGauss = 2048;
+constexpr int kCsMaxGauss = 16384;
+struct CsPlan {
+    int band_rows, n_bands, gauss, nb;
+};
+struct CsArgs {
+    long long n;           // emission positions (records)
+    int nb, gauss;         // blocks of `gauss` positions
+    int n_tiles, tiles_x, tiles_y;
+    int band_rows, n_bands;
+    const uint32_t *perm;  // position -> record, or nullptr
+    const uint2 *rect;     // per record: (tx0 | tx1 << 16, ty0 | ty1 << 16), view-local tiles
+    const uint32_t *count; // per position: tiles covered
+    uint16_t *hist;        // nb x n_tiles: instances of each tile in each block
+    uint32_t *off;         // nb x n_tiles: instances of the tile in earlier blocks
+    uint32_t *tile_tot;    // n_tiles
+    const uint2 *ranges;   // n_tiles: [start, end) (written by the schedule kernel)
+    uint32_t *vals;        // capacity: record ids in tile order
+    int *status;
+    int64_t capacity;
 };
 
 // A work item names an existing tile and a chunk k < m whose slots fit.
@@ -216,6 +252,12 @@ void launch_permute_counts(long long n, const uint32_t *perm, const uint32_t *co
                            uint32_t *block_sums, cudaStream_t s);
 // Blend work items from the tile ranges (one CTA).
 void launch_schedule(const ScheduleArgs &a, cudaStream_t s);
+// Band and block sizes of the counting sort; false where it does not apply
+// (several views, or a tile row longer than a band).
+bool cs_plan(int n_views, int tiles_x, int tiles_y, long long n, CsPlan &p);
+void launch_cs_count(const CsArgs &a, cudaStream_t s);
+void launch_cs_colscan(const CsArgs &a, cudaStream_t s);
+void launch_cs_emit(const CsArgs &a, cudaStream_t s);
 
 // Persistent blend kernels over the batch's (view, tile) items; return false
 // when (K, tile shape, px/thread) has no compiled instance.

@@ -102,3 +102,10 @@ def test_baked_record_size_matches_the_header():
         assert eval(expr, {"deg": deg}) == B.baked_floats(deg)
         assert B.baked_floats(deg) % 4 == 0 and B.baked_floats(deg) >= 12 + 3 * (deg + 1) ** 2
     assert B.baked_floats(3) * 4 == 240
+
+
+def test_static_scratch_size_matches_the_header():
+    from paper_2410_08129_gb300 import binding as B
+    hdr = open(os.path.join(ROOT, "include", "htgs.h")).read()
+    m = re.search(r"#define HTGS_STATIC_SCRATCH_BYTES \((\d+)u \* (\d+)u \* (\d+)u\)", hdr)
+    assert m and int(m.group(1)) * int(m.group(2)) * int(m.group(3)) == B.HTGS_STATIC_SCRATCH_BYTES
