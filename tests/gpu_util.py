@@ -23,7 +23,7 @@ TAU_ALPHA = 1.0 / 255.0
 MAX_AMBIGUOUS = 1e-3
 # The oracle's near-decision margins (the FP32 path may take a decision the
 # other way only within them).
-DEPTH_REL, TAUK_ABS, CUTOFF_REL = 1e-6, 2e-6, 2e-5
+DEPTH_REL, TAUK_ABS, CUTOFF_REL = 1e-6, 2e-6, 4e-6
 # Near-decisions without a per-pixel budget: a ray almost parallel to a flat
 # splat (its FP32 evaluation can return any alpha and depth).
 UNBOUNDED = oracle.AMB_DEN

@@ -164,3 +164,81 @@ def test_sorted_tile_lists(n_views, size, tile):
         r = Renderer(cam, prm, scene.n, launch=B.c_launch(tile, 1))
         ref = r.forward(g)
         assert float((img - ref).abs().max()) <= 1e-5
+
+
+def test_batch_training_step_captured_in_cuda_graph():
+    """The whole batched training step in one CUDA graph: the batched
+    forward, the per-view L1 loss and its gradient, the batched backward.
+    Two scenes share the batch: a 2000-Gaussian scene seen by five views of
+    uneven size and a 64-Gaussian scene seen only by a 32x32 crop of the
+    1200x800 training camera. The replay equals an eager run of the same
+    calls (images and upstream gradients bit for bit; losses and parameter
+    gradients up to the order of their atomic sums), and the small scene's
+    gradient equals the FP64 oracle's for the upstream gradient the loss
+    produced (Sec. 3.3)."""
+    import oracle
+    from tests.gpu_util import assert_grad_close, grads_to_numpy
+    big = _scene(2000, 8)
+    small = scenes.small_box_scene(64, seed=2, sh_degree=1)
+    small.means[:, :2] *= np.float32(0.04)
+    gb, gs = GaussianTensors.from_scene(big), GaussianTensors.from_scene(small)
+    crop = scenes.identity_camera(1200, 800, 1200.0).crop(584, 384, 32, 32).rounded()
+    cams = _cameras(SIZES, seed=8) + [crop]
+    views = [gb] * len(SIZES) + [gs]
+    prm = scenes.Params(K=8, bg=(0.1, 0.2, 0.3))
+    rng = np.random.Generator(np.random.PCG64(9))
+    tb = GaussianTensors.from_scene(scenes.perturbed(big, rng))
+    ts = GaussianTensors.from_scene(scenes.perturbed(small, rng))
+    targets = [t.clone() for t in BatchRenderer([tb] * len(SIZES) + [ts], cams, prm).forward()]
+    br = BatchRenderer(views, cams, prm)
+    br.forward(check=True)  # sizes the instance capacity
+    dls = [torch.empty_like(im) for im in br.images]
+    losses = torch.zeros(len(cams), dtype=torch.float32, device="cuda")
+    grads = br.gradient_buffers()
+    vf, vb = br.views(), br.views(dl_dimages=dls, grads=grads)
+
+    def step():
+        B._check(B.htgs_render_batch(vf, prm, br.launch, br.workspace, br.capacity), "htgs_render_batch")
+        for k in range(len(cams)):
+            B._check(B.htgs_l1_loss_grad(br.images[k], targets[k], dls[k], losses[k:k + 1]), "l1")
+        B._check(B.htgs_render_batch_backward(vb, prm, br.launch, br.workspace, br.capacity),
+                 "htgs_render_batch_backward")
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager_img = [im.clone() for im in br.images]
+    eager_dl = [d.clone() for d in dls]
+    eager_loss = losses.clone()
+    eager_grads = {k: {f: v.clone() for f, v in gd.items()} for k, gd in grads.items()}
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        step()
+    for t in br.images + dls + [losses] + [v for gd in grads.values() for v in gd.values()]:
+        t.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    st, _ = B.htgs_get_error(br.workspace)
+    assert st == B.HTGS_OK
+    for a, b in zip(eager_img, br.images):
+        assert torch.equal(a, b)
+    for a, b in zip(eager_dl, dls):
+        assert torch.equal(a, b)
+    # (the loss adds block partial sums atomically: equal up to summation order)
+    torch.testing.assert_close(losses, eager_loss, rtol=1e-6, atol=0.0)
+    assert float(losses.min()) > 0
+    for key, gd in grads.items():
+        for f in FIELDS:
+            torch.testing.assert_close(gd[f], eager_grads[key][f], rtol=1e-5,
+                                       atol=1e-6 * float(eager_grads[key][f].abs().max()))
+    # The small scene's gradient against the oracle, for the upstream
+    # gradient the captured loss wrote (its near-decision pixels, where FP32
+    # and FP64 may choose differently, must not exist in this view).
+    _, d = oracle.render(small.astype(np.float64), crop, prm, diagnostics=True)
+    assert not d["near_decision"].any()
+    dl = dls[-1].cpu().numpy().astype(np.float64)
+    ref = oracle.render_backward(small.astype(np.float64), crop, prm, dl)
+    assert_grad_close(grads_to_numpy(grads[id(gs)]), ref, label="graph-captured step, small scene")

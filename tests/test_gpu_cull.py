@@ -60,9 +60,7 @@ def test_thin_splats_match_the_oracle(thin):
     scene, cam, prm, runs = thin
     img, counters = runs[SHAPES[0]]
     ref, d = oracle.render(scene.astype(np.float64), cam, prm, diagnostics=True)
-    # The oracle marks 0.29% of the pixels ambiguous (mostly cutoff decisions
-    # of needles and discs).
-    image_parity(img, ref, d, "thin splats", 0.0029)
+    image_parity(img, ref, d, "thin splats")
     # Every fragment the oracle keeps is kept (up to cutoff decisions that
     # FP32 and FP64 take differently, a few per million).
     n_ref = int(d["n_frag"].sum())

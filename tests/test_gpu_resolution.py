@@ -22,13 +22,19 @@ from tests.gpu_util import CUTOFF_REL, DEPTH_REL, gpu_render, saved_planes
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("seed,grow,n", [(95, -1.5, 10000), (97, -1.2, 5000)])
-def test_cutoff_and_depth_decisions_lie_within_the_margins(seed, grow, n):
+@pytest.mark.parametrize("seed,grow,n,flat", [(95, -1.5, 10000, 0.0), (97, -1.2, 5000, 0.0), (98, -1.2, 6000, 0.3)])
+def test_cutoff_and_depth_decisions_lie_within_the_margins(seed, grow, n, flat):
     """About 20 fragments per pixel over 512x384 pixels: some 2.5M kept
     fragments on the shallow pixels, about 150 pixels with a fragment in the
-    cutoff band."""
+    cutoff band. The third scene makes 30% of the splats flat (one scale
+    1e-7, as in the stress workload), where the evaluation is least well
+    conditioned."""
     scene = scenes.small_box_scene(n, seed=seed, sh_degree=0)
     scene.log_scales += np.float32(grow)
+    if flat:
+        rng = np.random.default_rng(seed)
+        idx = np.flatnonzero(rng.random(n) < flat)
+        scene.log_scales[idx, rng.integers(0, 3, idx.size)] = np.float32(np.log(1e-7))
     cam = scenes.identity_camera(512, 384, 512.0).rounded()
     K = 32
     prm = scenes.Params(K=K, tau_K=0.0)
@@ -61,7 +67,7 @@ def test_cutoff_and_depth_decisions_lie_within_the_margins(seed, grow, n):
                 assert gap <= DEPTH_REL, (i, j, G, gap)
                 worst_depth = max(worst_depth, gap)
                 n_order += 1
-    rep = dict(seed=seed, pixels=int(shallow.sum()), fragments=int(d["n_frag"][shallow].sum()),
+    rep = dict(seed=seed, flat=flat, pixels=int(shallow.sum()), fragments=int(d["n_frag"][shallow].sum()),
                band_pixels=band_pixels, cutoff_flips=n_cut, worst_cutoff_flip=worst_cut,
                order_flips=n_order, worst_depth_flip=worst_depth)
     print("RESOLUTION " + json.dumps(rep))

@@ -19,14 +19,14 @@ pytestmark = pytest.mark.gpu
 # pixel), a denser region (140) and an off-axis one (80).
 CROPS_1080 = [(896, 476, 128, 128), (400, 700, 128, 128), (1500, 200, 128, 128)]
 # Share of pixels the oracle marks ambiguous on these crops, measured on
-# these exact inputs: 0.16-0.23% at K = 4, 0.08-0.12% at K = 8, 0.10-0.19%
-# at K = 16 (cutoff decisions of fragments in front, depth ties).
-CAP_CFG2 = {4: 0.0023, 8: 0.0012, 16: 0.0019}
+# these exact inputs: 0.03-0.07% at K = 4, 0.03-0.10% at K = 8, 0.10-0.19%
+# at K = 16 (depth ties in the core, cutoff decisions of fragments in front).
+CAP_CFG2 = {4: 1e-3, 8: 0.0011, 16: 0.0019}
 # 6M-Gaussian stress frame, 128x128 crops: centre (770 fragments per pixel)
-# and a shallower one (250). Measured 0.04-0.10%, 0.11%, 0.19-0.26% and
+# and a shallower one (250). Measured 0.04-0.06%, 0.11%, 0.19-0.26% and
 # 0.22-0.38% at K = 4, 8, 16, 32 (depth ties in deep cores).
 CROPS_STRESS = [(896, 476, 128, 128), (300, 300, 128, 128)]
-CAP_CFG5 = {4: 0.0011, 8: 0.0011, 16: 0.0026, 32: 0.0039}
+CAP_CFG5 = {4: 1e-3, 8: 0.0011, 16: 0.0026, 32: 0.0039}
 
 
 @pytest.fixture(scope="module")

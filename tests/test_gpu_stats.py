@@ -40,11 +40,13 @@ def test_statistics_match_oracle(K):
     got = {k: v.cpu().numpy().astype(np.float64) for k, v in st.items()}
     np.testing.assert_array_equal(got["densify_count"], ref["densify_count"])
     assert 0 < ref["densify_count"].sum() < scene.n
-    # visibility: FP32 weights; a near-decision at a Gaussian's heaviest pixel may move it further
+    # visibility: the largest FP32 blending weight of each Gaussian within
+    # 2e-4 + 2e-3 v of the FP64 one, for every Gaussian (measured: none
+    # misses, largest error 5e-7)
     vis_err = np.abs(got["visibility"] - ref["visibility"]) > 2e-4 + 2e-3 * ref["visibility"]
     print("STATS " + json.dumps(dict(K=K, vis_miss=float(vis_err.mean()), n_miss=int(vis_err.sum()),
                                      vis_max_err=float(np.abs(got["visibility"] - ref["visibility"]).max()))))
-    assert vis_err.mean() <= 0.03, (vis_err.sum(), np.abs(got["visibility"] - ref["visibility"]).max())
+    assert vis_err.sum() == 0, (vis_err.sum(), np.abs(got["visibility"] - ref["visibility"]).max())
     assert ref["visibility"].max() > 0.1
     # the densification statistic follows the mean gradient (1e-3 relative per tensor)
     gm = grads["means"].cpu().numpy().astype(np.float64)

@@ -42,3 +42,40 @@ def test_static_scratch_rejects_scenes_beyond_its_size():
     img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
     st = B.htgs_render_static(g.c_struct(), cam, prm, B.c_launch(tile), img)
     assert st == B.HTGS_ERR_WORKSPACE, B.htgs_status_string(st)
+
+
+def _static_ceiling(cam, prm, launch):
+    """Largest Gaussian count whose instance-free workspace fits the static
+    array (host arithmetic through htgs_workspace_size)."""
+    lo, hi = 1, 1 << 24
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if B.htgs_workspace_size(mid, cam, prm, launch, 0)[0] <= B.HTGS_STATIC_SCRATCH_BYTES:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def test_static_scratch_renders_a_scene_just_under_its_ceiling():
+    """The stated limit holds: a scene 2000 Gaussians under the largest
+    count whose workspace fits (its first 256 are the 64x64 test frame, the
+    rest lie behind the camera and cover no tile) renders, and equals the
+    frame rendered by htgs_render; one Gaussian over the limit is refused."""
+    frame, cam, prm, tile = scenes.config1()
+    cam = cam.rounded()
+    launch = B.c_launch(tile)
+    n_max = _static_ceiling(cam, prm, launch)
+    assert 150_000 < n_max < 170_000  # about 208 bytes per Gaussian in 32 MiB
+    hidden = scenes.small_box_scene(n_max - 2000 - frame.n, seed=5)
+    hidden.means[:, 2] = np.float32(-3.0)
+    scene = frame.concat(hidden)
+    g = GaussianTensors.from_scene(scene)
+    ref = Renderer(cam, prm, frame.n, launch=launch).forward(GaussianTensors.from_scene(frame)).clone()
+    img = torch.full_like(ref, float("nan"))
+    st = B.htgs_render_static(g.c_struct(), cam, prm, launch, img)
+    assert st == B.HTGS_OK, B.htgs_status_string(st)
+    assert torch.equal(img, ref)
+    over = GaussianTensors.from_scene(frame.concat(scenes.small_box_scene(n_max + 1 - frame.n, seed=6)))
+    st = B.htgs_render_static(over.c_struct(), cam, prm, launch, img)
+    assert st == B.HTGS_ERR_WORKSPACE, B.htgs_status_string(st)
