@@ -689,7 +689,7 @@ def main():
         assert ksr.status()[0] == B.HTGS_OK
         kms = max_over_ranks(w0.elapsed_time(w1))
         k_sweep[str(kk)] = {"value": job_throughput(args.steps, world, kms), "unit": UNIT,
-                            "ms_per_step": kms / args.steps}
+                            "ms_per_step": kms / args.steps, "counters": B.htgs_get_counters(ksr.workspace)}
         del ksr, ksimg
 
     # ---- the same frame rendered without the tail (inference variant) ------
