@@ -40,6 +40,9 @@ typedef int32_t htgs_status;
 #define HTGS_ERR_CUDA 4          /* a CUDA launch or runtime call failed */
 #define HTGS_ERR_TIMEOUT 5       /* a bounded device-side wait gave up */
 #define HTGS_ERR_NOT_SUPPORTED 6 /* e.g. K above the largest compiled core size */
+#define HTGS_ERR_INTERNAL 7      /* a device-side consistency check failed (the binning's tile
+                                    spans disagreed with the instance counts); the blend is
+                                    skipped */
 
 /* Largest core size K compiled into the blend kernels. */
 #define HTGS_MAX_K 32
@@ -155,8 +158,14 @@ typedef struct {
                                  covering each tile in record order, or in mean-depth order for
                                  sorted blending): 0 (default) or 1 the stable LSD radix sort of
                                  tile keys; 2 a stable counting sort by tile computed from the
-                                 records' tile rectangles, for a single view whose tile rows are
+                                 records' tile covers, for a single view whose tile rows are
                                  at most 2048 tiles long (HTGS_ERR_NOT_SUPPORTED otherwise) */
+    int32_t tile_cover;       /* which tiles a Gaussian is binned to (Sec. 4.3); both give the
+                                 same image up to the summation order of split tiles: 0
+                                 (default) per tile row of its bounding rectangle the span of
+                                 tiles its cutoff ellipse reaches (the ellipse holds every pixel
+                                 with rho^2 <= rho_c, so no tile with a fragment is dropped);
+                                 1 every tile of the rectangle */
 } htgs_launch;
 
 /* Sizes of the caller-owned buffers for one camera.
@@ -172,8 +181,8 @@ htgs_status htgs_workspace_size(int64_t n_gaussians, const htgs_camera *cam,
 /* Byte offsets of the internal buffers inside a workspace, for inspection by
  * tests and tools; their contents are valid after htgs_render has run.
  *   rec          n x 8 float4: per-Gaussian blend record (128 bytes)
- *   rect         n x uint2: covered tiles (tx0 | tx1 << 16, ty0 | ty1 << 16)
- *   count        n x uint32: covered tile count
+ *   rect         n x uint2: bounding tile rectangle (tx0 | tx1 << 16, ty0 | ty1 << 16)
+ *   count        n x uint32: tiles the Gaussian is binned to (htgs_launch.tile_cover)
  *   sorted_keys  capacity x uint32: tile keys after the radix sort
  *   sorted_vals  capacity x uint32: the matching Gaussian ids
  *   ranges       n_tiles x uint2: [start, end) of each tile in the sorted list
@@ -322,9 +331,9 @@ htgs_status htgs_l1_loss_grad(const float *image, const float *target, int64_t n
  * has no counterpart of this entry point.
  *   image   [out] height x width x 3 float32, device (caller-owned)
  * Size limit: the workspace of htgs_workspace_size must fit the array. That
- * is about 208 bytes per Gaussian (the blend record, tile rectangle and
- * count, and the per-Gaussian accumulators the layout keeps) plus a small
- * per-tile part, so at most about 161,000 Gaussians even with no tile
+ * is about 240 bytes per Gaussian (the blend record, tile rectangle, tile
+ * cover and count, and the per-Gaussian accumulators the layout keeps) plus
+ * a small per-tile part, so at most about 139,000 Gaussians even with no tile
  * instances; the rest of the array holds the instances, at about
  * 18 + (6 + 2K) * tile_pixels / 128 bytes each (44 at K = 4 with 16x16
  * tiles). Beyond the first limit the call returns HTGS_ERR_WORKSPACE, beyond

@@ -24,6 +24,7 @@ HTGS_ERR_OVERFLOW = 3
 HTGS_ERR_CUDA = 4
 HTGS_ERR_TIMEOUT = 5
 HTGS_ERR_NOT_SUPPORTED = 6
+HTGS_ERR_INTERNAL = 7
 HTGS_MAX_K = 32
 HTGS_MAX_CAPACITY = (1 << 31) - 1
 HTGS_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -64,7 +65,8 @@ class Launch(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("px_per_thread", ctypes.c_int32), ("depth_bits", ctypes.c_int32),
                 ("smem_batch", ctypes.c_int32), ("events", ctypes.c_void_p * 6),
-                ("test_lookback_stall", ctypes.c_int32), ("binning", ctypes.c_int32)]
+                ("test_lookback_stall", ctypes.c_int32), ("binning", ctypes.c_int32),
+                ("tile_cover", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):
@@ -161,15 +163,19 @@ def c_params(p) -> Params:
 
 
 BINNING_AUTO, BINNING_RADIX, BINNING_COUNTING = 0, 1, 2
+# htgs_launch.tile_cover: the tiles of the rectangle the cutoff ellipse reaches
+# (row by row), or every tile of the rectangle.
+COVER_ELLIPSE, COVER_RECT = 0, 1
 
 
 def c_launch(tile=(16, 16), px_per_thread=0, depth_bits=0, events=None, smem_batch=0,
-             test_lookback_stall=0, binning=BINNING_AUTO) -> Launch:
+             test_lookback_stall=0, binning=BINNING_AUTO, tile_cover=COVER_ELLIPSE) -> Launch:
     """events: up to 6 torch.cuda.Event(enable_timing=True) (or None) recorded
     around the render phases, see htgs_launch in include/htgs.h."""
     L = Launch(int(tile[0]), int(tile[1]), int(px_per_thread), int(depth_bits), int(smem_batch))
     L.test_lookback_stall = int(test_lookback_stall)
     L.binning = int(binning)
+    L.tile_cover = int(tile_cover)
     for i, e in enumerate(events or []):
         L.events[i] = e.cuda_event if e is not None else None
     return L

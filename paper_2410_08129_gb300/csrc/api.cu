@@ -30,7 +30,7 @@ struct Layout {
     size_t d_ghist, d_tickets, d_lookback, zero_end;  // depth sort (sorted blending)
     size_t dkeys0, dvals0, dkeys1, dvals1, count_p, block_sums_p;
     int sorted, n_dsort_blocks;
-    size_t rec, rect, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, vis, end;
+    size_t rec, rect, cover, count, block_sums, keys0, vals0, keys1, vals1, items, partials, bwd_work, acc, vis, end;
     int n_blocks, n_sort_blocks, passes, digit_bits, slots_cap, max_items;
     // Counting-sort binning (used when `cs`): per-block tile counts and
     // offsets, per-tile totals.
@@ -46,6 +46,7 @@ bool tile_shape(const htgs_launch *launch, TileArgs &t) {
     t.tile_h = (launch && launch->tile_h) ? launch->tile_h : 16;
     t.depth_bits = launch ? launch->depth_bits : 0;
     t.batch = (launch && launch->smem_batch) ? launch->smem_batch : 128;
+    t.cover = launch ? launch->tile_cover : 0;
     const bool shape_ok = (t.tile_w == 16 && t.tile_h == 16) || (t.tile_w == 16 && t.tile_h == 8) ||
                           (t.tile_w == 8 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 16);
     const bool batch_ok = t.batch == 32 || t.batch == 64 || t.batch == 128;
@@ -62,6 +63,7 @@ htgs_status params_ok(const htgs_params *prm, const htgs_launch *launch) {
     if (!(prm->tau_alpha > 0.f) || !(prm->alpha_max < 1.f) || !(prm->alpha_max > 0.f))
         return HTGS_ERR_INVALID_ARG;
     if (launch && (launch->px_per_thread < 0 || launch->px_per_thread > 4)) return HTGS_ERR_INVALID_ARG;
+    if (launch && (launch->tile_cover < 0 || launch->tile_cover > 1)) return HTGS_ERR_INVALID_ARG;
     return HTGS_OK;
 }
 
@@ -129,6 +131,7 @@ htgs_status make_layout(int n_views, const HostView *views, const htgs_params *p
     L.zero_end = o;
     L.rec = o; o = align_up(o + (size_t)n_rec * kRecF4 * sizeof(float4));
     L.rect = o; o = align_up(o + (size_t)n_rec * sizeof(uint2));
+    L.cover = o; o = align_up(o + (size_t)n_rec * 2 * sizeof(uint4));
     L.count = o; o = align_up(o + (size_t)n_rec * sizeof(uint32_t));
     L.block_sums = o; o = align_up(o + (size_t)(L.n_blocks + 1) * sizeof(uint32_t));
     const size_t dn = dsort ? (size_t)n_rec : 0;
@@ -296,6 +299,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
         pre.prm = pa; pre.tiles = L.tiles;
         pre.rec = at<float4>(workspace, L.rec);
         pre.rect = at<uint2>(workspace, L.rect);
+        pre.cover = at<uint4>(workspace, L.cover);
         pre.count = at<uint32_t>(workspace, L.count);
         pre.block_sums = at<uint32_t>(workspace, L.block_sums);
         pre.stats = at<unsigned long long>(workspace, L.stats);
@@ -313,6 +317,8 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     BinArgs bin{};
     bin.n = L.n_rec; bin.n_blocks = L.n_blocks;
     bin.rect = at<uint2>(workspace, L.rect);
+    bin.cover = at<uint4>(workspace, L.cover);
+    bin.tile_w = L.tiles.tile_w; bin.tile_h = L.tiles.tile_h; bin.use_ellipse = L.tiles.cover == 0;
     bin.count = at<uint32_t>(workspace, L.count);
     bin.block_sums = at<uint32_t>(workspace, L.block_sums);
     if (L.sorted && L.n_blocks > 0) {
@@ -355,6 +361,7 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
         ca.n_tiles = L.tiles.n_tiles; ca.tiles_x = b.v[0].tiles_x; ca.tiles_y = b.v[0].tiles_y;
         ca.band_rows = L.csp.band_rows; ca.n_bands = L.csp.n_bands;
         ca.perm = bin.perm; ca.rect = bin.rect; ca.count = bin.count;
+        ca.cover = bin.cover; ca.tile_w = bin.tile_w; ca.tile_h = bin.tile_h; ca.use_ellipse = bin.use_ellipse;
         ca.hist = at<uint16_t>(workspace, L.cs_hist);
         ca.off = at<uint32_t>(workspace, L.cs_off);
         ca.tile_tot = at<uint32_t>(workspace, L.cs_tot);
@@ -518,6 +525,7 @@ const char *htgs_status_string(htgs_status s) {
     case HTGS_ERR_CUDA: return "CUDA error";
     case HTGS_ERR_TIMEOUT: return "bounded device wait gave up";
     case HTGS_ERR_NOT_SUPPORTED: return "configuration not supported";
+    case HTGS_ERR_INTERNAL: return "device-side consistency check failed";
     default: return "unknown status";
     }
 }

@@ -3,8 +3,9 @@
 // depth sort).
 //
 //   scan_blocks  exclusive scan of the preprocess block sums; overflow check
-//   emit         one thread group per Gaussian writes (tile key, gid) for each
-//                covered tile, load-balanced across the lanes of a warp
+//   emit         (tile key, gid) for each tile a Gaussian covers (per tile row
+//                of its rectangle, the span its cutoff ellipse reaches),
+//                load-balanced across the lanes of a warp
 //   histogram    digit histograms of every radix pass in one read of the keys
 //   onesweep     one stable scatter per digit (the key bits split evenly into
 //                the fewest passes of at most 9 bits); the block prefix comes
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(BinArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Emit: instance j of Gaussian g covers tile (tx0 + r % w, ty0 + r / w).
+// Emit: the instances of a Gaussian are its cover's tiles, row by row.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant__ Batch b, BinArgs a) {
     __shared__ uint32_t warp_tot[kPreThreads / 32];
@@ -111,49 +112,44 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
         vtx = (uint32_t)V.tiles_x;
         vtoff = (uint32_t)V.tile_off;
     }
-    uint32_t incl = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const uint32_t excl = incl - c;
-    const uint32_t wtot = __shfl_sync(kFull, incl, 31);
+    uint32_t wtot;
+    warp_excl_scan(c, lane, &wtot);
     if (lane == 0) warp_tot[warp] = wtot;
     __syncthreads();
     uint32_t woff = 0;
     for (int w = 0; w < warp; ++w) woff += warp_tot[w];
     const uint64_t base = (uint64_t)a.block_sums[blockIdx.x] + woff;
-    const uint2 r = c ? a.rect[rec] : make_uint2(0u, 0u);
-    const int iters = (int)((wtot + 31) / 32);
-    for (int it = 0; it < iters; ++it) {
-        const uint32_t j = (uint32_t)it * 32 + lane;
-        // Owner lane: the largest l with excl[l] <= j (lanes with no instances
-        // share their offset with the next lane that has some).
-        int L = 0;
-        for (int step = 16; step >= 1; step >>= 1) {
-            const int cand = L + step;
-            const uint32_t v = __shfl_sync(kFull, excl, cand);
-            if (v <= j) L = cand;
-        }
-        const uint32_t rx = __shfl_sync(kFull, r.x, L);
-        const uint32_t ry = __shfl_sync(kFull, r.y, L);
-        const uint32_t eL = __shfl_sync(kFull, excl, L);
-        const uint32_t ltx = __shfl_sync(kFull, vtx, L);
-        const uint32_t ltoff = __shfl_sync(kFull, vtoff, L);
-        const uint32_t lrec = __shfl_sync(kFull, rec, L);
-        if (j < wtot) {
-            const uint32_t rr = j - eL;
-            const uint32_t tx0 = rx & 0xffffu, tx1 = rx >> 16;
-            const uint32_t w = tx1 - tx0 + 1;
-            const uint32_t tx = tx0 + rr % w;
-            const uint32_t ty = (ry & 0xffffu) + rr / w;
-            const uint64_t pos = base + j;
-            if (pos < (uint64_t)a.capacity) {
-                a.keys[pos] = ltoff + ty * ltx + tx;
-                a.vals[pos] = lrec;
-            }
-        }
-    }
+    // The lane's own cover (only read for a record that emits something).
+    const RowCover cov = c ? load_cover(a.cover, rec, a.use_ellipse != 0)
+                           : row_cover(make_uint2(1u, 0u), 0.f, 0.f, 0.f, 0.f, 0.f, false);
+    const uint32_t lo = c ? cov.ty0 : 1u, hi = c ? cov.ty1 : 0u;
+    const uint64_t cap = (uint64_t)a.capacity;
+    // The warp deals out its (record, row) pairs 32 at a time; each lane
+    // writes the span of its row (rows are a few tiles wide, so the lanes
+    // stay nearly in step and neighbouring lanes write neighbouring slots).
+    uint32_t run = 0;
+    warp_cover_rows(cov, lo, hi, lane, a.tile_w, a.tile_h,
+                    [&](bool, uint32_t owner, uint32_t row, uint32_t s0, uint32_t w) {
+                        uint32_t tot;
+                        const uint32_t off = run + warp_excl_scan(w, lane, &tot);
+                        const uint32_t ltx = __shfl_sync(kFull, vtx, (int)owner);
+                        const uint32_t ltoff = __shfl_sync(kFull, vtoff, (int)owner);
+                        const uint32_t lrec = __shfl_sync(kFull, rec, (int)owner);
+                        const uint32_t key0 = ltoff + row * ltx + s0;
+                        for (uint32_t t = 0; t < w; ++t) {
+                            // (off + t < wtot: never past this warp's share of the list.)
+                            const uint64_t pos = base + off + t;
+                            if (off + t < wtot && pos < cap) {
+                                a.keys[pos] = key0 + t;
+                                a.vals[pos] = lrec;
+                            }
+                        }
+                        run += tot;
+                    });
+    // The spans are the ones the preprocess counted (same steps, same
+    // inputs); a mismatch would leave slots unwritten, so it is reported
+    // and the blend is skipped.
+    if (lane == 0 && run != wtot) set_error(a.status, HTGS_ERR_INTERNAL);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,6 +86,7 @@ struct PreArgs {
     uint32_t *dtotal;      // sorted blending: receives n_rec (the depth sort's length)
     float4 *rec;           // n_rec * kRecF4
     uint2 *rect;           // n_rec: (tx0 | tx1 << 16, ty0 | ty1 << 16), view-local tiles
+    uint4 *cover;          // n_rec * 2: the record's cover (see CoverRec)
     uint32_t *count;       // n_rec
     uint32_t *block_sums;  // ceil(n_rec / kPreThreads)
     unsigned long long *stats;
@@ -105,6 +106,8 @@ struct BinArgs {
     int n_blocks;          // ceil(n / kPreThreads)
     const uint32_t *perm;  // emission order of the records (position -> record), or nullptr
     const uint2 *rect;
+    const uint4 *cover;    // per record: its cover (see CoverRec)
+    int tile_w, tile_h, use_ellipse;  // tile shape; TileArgs::cover == 0
     const uint32_t *count; // per position (permuted when perm is set)
     uint32_t *block_sums;  // in: per-block sums; out: exclusive block offsets
     int *status;
@@ -172,6 +175,8 @@ struct CsArgs {
     int band_rows, n_bands;
     const uint32_t *perm;  // position -> record, or nullptr
     const uint2 *rect;     // per record: (tx0 | tx1 << 16, ty0 | ty1 << 16), view-local tiles
+    const uint4 *cover;    // per record: its cover (see CoverRec)
+    int tile_w, tile_h, use_ellipse;  // tile shape; TileArgs::cover == 0
     const uint32_t *count; // per position: tiles covered
     uint16_t *hist;        // nb x n_tiles: instances of each tile in each block
     uint32_t *off;         // nb x n_tiles: instances of the tile in earlier blocks

@@ -3,7 +3,8 @@
 // screen bounding box and the opacity-aware cutoff).
 //
 // One thread per Gaussian. The forward writes the 128-byte blend record (see
-// common.cuh), the covered tile rectangle and the tile count; the backward
+// common.cuh), the bounding tile rectangle and the instance count (the
+// tiles of the rectangle the cutoff ellipse reaches, row by row); the backward
 // turns the per-Gaussian gradient accumulators of the blend adjoint into
 // gradients of the means, log-scales, quaternions, opacity logits and SH.
 #include "common.cuh"
@@ -346,6 +347,10 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     uint32_t count = 0;
     unsigned long long box_pixels = 0;
+    // The record's cover and its tile rows (none unless it covers a tile).
+    RowCover rcov = row_cover(make_uint2(1u, 0u), 0.f, 0.f, 0.f, 0.f, 0.f, false);
+    uint32_t row_lo = 1u, row_hi = 0u;
+    float mu_z = 0.f;
     if (i < b.n_rec) {
         // Record i is Gaussian g of the scene that view v renders.
         const ViewDesc &V = b.v[view_of_record(b, i)];
@@ -398,7 +403,6 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
                 const uint32_t tx0 = (uint32_t)lo[0] / a.tiles.tile_w, tx1 = (uint32_t)hi[0] / a.tiles.tile_w;
                 const uint32_t ty0 = (uint32_t)lo[1] / a.tiles.tile_h, ty1 = (uint32_t)hi[1] / a.tiles.tile_h;
                 rect = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
-                count = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
                 // Record: quadratic coefficients about the box centre.
                 const float xc = pc[0], yc = pc[1];
                 Expansion E;
@@ -458,11 +462,40 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
 #pragma unroll
         for (int k = 0; k < kRecF4; ++k) slab[lane * kRecF4 + (k ^ (lane & 7))] = rec[k];
         a.rect[i] = rect;
+        mu_z = S.mu[2];
+        if ((rect.x & 0xffffu) <= (rect.x >> 16)) {
+            // The cover from the record's words (read back from the slab, so
+            // the record's registers are free by now), stored for the binning.
+            const float4 w4 = slab[lane * kRecF4 + (4 ^ (lane & 7))];
+            const float4 w7 = slab[lane * kRecF4 + (7 ^ (lane & 7))];
+            store_cover(a.cover, i, rect, w4.z, w4.w, w7.y, w7.z, w7.w);
+            rcov = row_cover(rect, w4.z, w4.w, w7.y, w7.z, w7.w, a.tiles.cover == 0);
+            row_lo = rect.y & 0xffffu;
+            row_hi = rect.y >> 16;
+        }
+    }
+    // Instances: per tile row of the rectangle, the tiles the ellipse reaches
+    // (or the whole row). The warp deals out its (record, row) pairs 32 at a
+    // time, so a splat with many rows does not hold up the other lanes.
+    {
+        __shared__ uint32_t s_cnt[kPreThreads];
+        const int lane = threadIdx.x & 31;
+        uint32_t *const wc = s_cnt + (threadIdx.x & ~31);
+        wc[lane] = 0;
+        __syncwarp();
+        warp_cover_rows(rcov, row_lo, row_hi, lane, a.tiles.tile_w, a.tiles.tile_h,
+                        [&](bool valid, uint32_t owner, uint32_t, uint32_t, uint32_t w) {
+                            if (valid && w) atomicAdd(&wc[owner], w);
+                        });
+        __syncwarp();
+        count = wc[lane];
+    }
+    if (i < b.n_rec) {
         a.count[i] = count;
         // Sorted blending: key = view-space mean depth (positive, so its float
         // bits order like the depth); records that emit nothing go last.
         if (a.dkey) {
-            a.dkey[i] = count ? __float_as_uint(S.mu[2]) : 0xffffffffu;
+            a.dkey[i] = count ? __float_as_uint(mu_z) : 0xffffffffu;
             a.dval[i] = (uint32_t)i;
             if (i == 0) *a.dtotal = (uint32_t)b.n_rec;
         }

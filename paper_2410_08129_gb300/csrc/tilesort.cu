@@ -2,12 +2,13 @@
 // by tile id (arXiv 2410.08129, Sec. 4.3: one instance per covered
 // (Gaussian, tile), keyed by the tile id only; no global depth sort).
 //
-// The instances of a record are the tiles of its rectangle, so no (key,
-// value) list is materialised: positions are computed from the rectangles.
+// The instances of a record are the tiles of its cover (per tile row of its
+// rectangle, the span its cutoff ellipse reaches), so no (key, value) list is
+// materialised: positions are computed from the covers.
 // Emission positions (records, or their mean-depth order for sorted
 // blending) are cut into blocks of `gauss` consecutive positions, and the
 // tile rows into bands of at most kCsBandTiles tiles. A CTA works on one
-// (block, band) pair and sees only the part of each rectangle inside its band.
+// (block, band) pair and sees only the rows of each cover inside its band.
 //
 //   cs_count    per (block, band): how many of the block's records cover each
 //               tile of the band (shared-memory atomics), written to a row of
@@ -43,40 +44,28 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// One emission position, restricted to the band: its instances in the band,
-// the first column and width of its rectangle, its first row in the band
-// (relative to the band's first row), and its record.
+// One emission position, restricted to the band: its cover and the cover's
+// rows [lo, hi] inside the band (lo > hi: none), and its record.
 struct PosInfo {
-    uint32_t c, tx0, w, r0, rec;
-    float rw;  // 1 / w, rounded: the row of instance rr is estimated as rr * rw and corrected
+    uint32_t lo, hi, rec;
+    RowCover cov;
 };
 
-__device__ __forceinline__ PosInfo band_part(uint32_t count, uint2 r, uint32_t rec, int band_r0, int band_r1) {
-    PosInfo q{0u, 0u, 1u, 0u, rec, 1.f};
+__device__ __forceinline__ PosInfo band_part(const CsArgs &a, uint32_t count, uint2 r, uint32_t rec, int band_r0,
+                                             int band_r1) {
+    PosInfo q;
+    q.lo = 1u; q.hi = 0u; q.rec = rec;
+    q.cov = row_cover(make_uint2(1u, 0u), 0.f, 0.f, 0.f, 0.f, 0.f, false);
     if (count) {
         const int ty0 = (int)(r.y & 0xffffu), ty1 = (int)(r.y >> 16);
         const int lo = max(ty0, band_r0), hi = min(ty1, band_r1 - 1);
         if (lo <= hi) {
-            q.tx0 = r.x & 0xffffu;
-            q.w = (r.x >> 16) - q.tx0 + 1;
-            q.r0 = (uint32_t)(lo - band_r0);
-            q.c = (uint32_t)(hi - lo + 1) * q.w;
-            q.rw = __frcp_rn((float)q.w);
+            q.cov = load_cover(a.cover, rec, a.use_ellipse != 0);
+            q.lo = (uint32_t)lo;
+            q.hi = (uint32_t)hi;
         }
     }
     return q;
-}
-
-// (rr / w, rr % w) for rr < 2^22 and 1 <= w < 2^16: the float estimate
-// rr * rw is within one of the quotient there, so one correction step in
-// either direction makes it exact.
-__device__ __forceinline__ void div_small(uint32_t rr, uint32_t w, float rw, uint32_t &qo, uint32_t &ro) {
-    int q = __float2int_rz(__fmul_rn((float)rr, rw));
-    int rem = (int)rr - q * (int)w;
-    if (rem < 0) { --q; rem += (int)w; }
-    else if (rem >= (int)w) { ++q; rem -= (int)w; }
-    qo = (uint32_t)q;
-    ro = (uint32_t)rem;
 }
 
 // The warp's positions [first, first + per_warp), kCsUnroll steps of 32 at a
@@ -104,7 +93,7 @@ __device__ __forceinline__ void for_warp_positions(const CsArgs &a, long long fi
 #pragma unroll
         for (int u = 0; u < kCsUnroll; ++u) {
             if (s0 + 32 * u < per_warp && first + s0 + 32 * u < a.n)
-                fn(band_part(cnt[u], rct[u], rec[u], band_r0, band_r1));
+                fn(band_part(a, cnt[u], rct[u], rec[u], band_r0, band_r1));
         }
     }
 }
@@ -114,41 +103,13 @@ __device__ __forceinline__ void for_warp_positions(const CsArgs &a, long long fi
 // order: position by position, each position's tiles row by row. Every lane
 // makes the same number of calls (padding slots with valid = false).
 template <class F>
-__device__ __forceinline__ void warp_instances(const PosInfo &q, int lane, int tiles_x, F &&f) {
-    if (__ballot_sync(kFull, q.c != 0) == 0) return;  // no instance of these positions in the band
-    uint32_t incl = q.c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const uint32_t excl = incl - q.c;
-    const uint32_t wtot = __shfl_sync(kFull, incl, 31);
-    for (uint32_t base = 0; base < wtot; base += 32) {
-        const uint32_t j = base + (uint32_t)lane;
-        // Owner: the largest lane l with excl[l] <= j (lanes without
-        // instances share their offset with the next lane that has some).
-        int L = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t v = __shfl_sync(kFull, excl, L + step);
-            if (v <= j) L += step;
-        }
-        const uint32_t eL = __shfl_sync(kFull, excl, L);
-        const uint32_t tx0 = __shfl_sync(kFull, q.tx0, L);
-        const uint32_t w = __shfl_sync(kFull, q.w, L);
-        const float rw = __shfl_sync(kFull, q.rw, L);
-        const uint32_t r0 = __shfl_sync(kFull, q.r0, L);
-        const uint32_t rec = __shfl_sync(kFull, q.rec, L);
-        const bool valid = j < wtot;
-        uint32_t tile = 0;
-        if (valid) {
-            uint32_t row, col;
-            div_small(j - eL, w, rw, row, col);
-            tile = (r0 + row) * (uint32_t)tiles_x + tx0 + col;
-        }
-        f(valid, tile, rec);
-    }
+__device__ __forceinline__ void warp_instances(const CsArgs &a, const PosInfo &q, int lane, int band_r0, F &&f) {
+    if (__ballot_sync(kFull, q.lo <= q.hi) == 0) return;  // no row of these positions in the band
+    warp_cover_instances(q.cov, q.lo, q.hi, lane, a.tile_w, a.tile_h,
+                         [&](bool valid, uint32_t, uint32_t ty, uint32_t tx, uint32_t owner) {
+                             const uint32_t rec = __shfl_sync(kFull, q.rec, (int)owner);
+                             f(valid, (ty - (uint32_t)band_r0) * (uint32_t)a.tiles_x + tx, rec);
+                         });
 }
 
 struct Band {
@@ -174,7 +135,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_count_kernel(CsArgs a) {
     const int per_warp = a.gauss / kCsWarps;
     const long long first = (long long)blockIdx.x * a.gauss + (long long)warp * per_warp;
     for_warp_positions(a, first, per_warp, lane, B.r0, B.r1, [&](const PosInfo &q) {
-        warp_instances(q, lane, a.tiles_x, [&](bool valid, uint32_t tile, uint32_t) {
+        warp_instances(a, q, lane, B.r0, [&](bool valid, uint32_t tile, uint32_t) {
             if (valid && tile < (uint32_t)B.nt) atomicAdd(&s_hist[tile], 1u);
         });
     });
@@ -235,7 +196,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_emit_kernel(CsArgs a) {
     uint32_t *const wc = s_wc[warp >> 1];
     const uint32_t shift = (warp & 1) ? 16u : 0u;
     for_warp_positions(a, first, per_warp, lane, B.r0, B.r1, [&](const PosInfo &q) {
-        warp_instances(q, lane, a.tiles_x, [&](bool valid, uint32_t tile, uint32_t) {
+        warp_instances(a, q, lane, B.r0, [&](bool valid, uint32_t tile, uint32_t) {
             if (valid && tile < (uint32_t)B.nt) atomicAdd(&wc[tile], 1u << shift);
         });
     });
@@ -257,7 +218,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_emit_kernel(CsArgs a) {
     __syncthreads();
     const uint32_t cap = a.capacity < 0xffffffffll ? (uint32_t)a.capacity : 0xffffffffu;
     for_warp_positions(a, first, per_warp, lane, B.r0, B.r1, [&](const PosInfo &q) {
-        warp_instances(q, lane, a.tiles_x, [&](bool valid, uint32_t tile, uint32_t rec) {
+        warp_instances(a, q, lane, B.r0, [&](bool valid, uint32_t tile, uint32_t rec) {
             const bool ok = valid && tile < (uint32_t)B.nt;
             const uint32_t vmask = __ballot_sync(kFull, ok);
             if (ok) {

@@ -49,9 +49,10 @@ def test_library_loads_and_host_entry_points_work(lib_path):
     lay = B.htgs_workspace_layout(256, cam, prm, B.c_launch(tile), 1 << 16)
     assert lay.n_tiles == 16 and lay.tiles_x == 4 and lay.tile_bits == 4
     assert B.htgs_status_string(B.HTGS_ERR_OVERFLOW) != B.htgs_status_string(B.HTGS_OK)
+    assert "unknown" not in B.htgs_status_string(B.HTGS_ERR_INTERNAL)
 
 
-@pytest.mark.parametrize("bad", ["K", "capacity", "tile", "batch", "n", "alpha_max", "size"])
+@pytest.mark.parametrize("bad", ["K", "capacity", "tile", "batch", "n", "alpha_max", "size", "cover"])
 def test_host_side_argument_checks(lib_path, bad):
     from paper_2410_08129_gb300 import binding as B
     _, cam, prm, tile = scenes.config1()
@@ -70,6 +71,9 @@ def test_host_side_argument_checks(lib_path, bad):
         expect = B.HTGS_ERR_NOT_SUPPORTED
     elif bad == "n":
         n = -1
+        expect = B.HTGS_ERR_INVALID_ARG
+    elif bad == "cover":
+        launch = B.c_launch(tile, tile_cover=2)
         expect = B.HTGS_ERR_INVALID_ARG
     elif bad == "alpha_max":
         prm = scenes.Params(alpha_max=1.0)

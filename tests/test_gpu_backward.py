@@ -85,8 +85,12 @@ def test_autograd_function_matches_direct_call():
     g2 = GaussianTensors.from_scene(scene)
     r2.forward(g2)
     direct = r2.backward(g2, dl)
+    # The adjoint adds each (record, tile) partial into the record's
+    # accumulators with float atomics, in an order that varies between runs:
+    # agreement up to that reordering, relative to the field's largest entry.
     for f in FIELDS:
-        torch.testing.assert_close(getattr(g, f).grad, direct[f], rtol=1e-5, atol=1e-6)
+        ref = direct[f]
+        torch.testing.assert_close(getattr(g, f).grad, ref, rtol=1e-5, atol=1e-5 * float(ref.abs().max()))
 
 
 @pytest.fixture(scope="module")

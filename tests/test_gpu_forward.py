@@ -41,36 +41,58 @@ def test_config1_core_ids_match(cfg1):
     assert np.abs(sv["T_core"][ok] - d["T_core"][ok]).max() <= 1e-5
 
 
+def _gpu_tile_lists(r, scene_n, cam, prm):
+    """Per-tile record lists of the last render, and the records' tile rectangles."""
+    lay = B.htgs_workspace_layout(scene_n, cam, prm, r.launch, r.capacity)
+    rect = workspace_view(r, lay.rect, 2 * scene_n, torch.int32).view(scene_n, 2).cpu().numpy().view(np.uint32)
+    ranges = workspace_view(r, lay.ranges, 2 * lay.n_tiles, torch.int32).view(-1, 2).cpu().numpy()
+    total = int(r.last_instances)
+    vals = workspace_view(r, lay.sorted_vals, max(total, 1), torch.int32).cpu().numpy()[:total]
+    lists = [vals[a:b] if b > a else vals[:0] for a, b in ranges]
+    return lists, rect, lay
+
+
 def test_config1_binning_matches_oracle(cfg1):
-    """Tile lists: GPU sorted lists equal the oracle's binning of the GPU's
-    own rectangles (bit-exact), and every oracle-covered pixel lies in a
-    tile the GPU emitted for that Gaussian."""
+    """Tile lists (Sec. 4.3). With the whole-rectangle cover they equal the
+    oracle's binning of the GPU's own rectangles bit for bit. With the
+    default ellipse cover each list is the rectangle list with some records
+    left out, in the same (ascending gid) order, and no record is left out of
+    a tile holding a pixel that the FP64 oracle puts clearly inside its cutoff
+    (rho^2 below rho_c by more than the near-decision margin 4e-6 max(1, rho_c)).
+    The oracle's covered pixel rectangle lies inside the GPU's tiles."""
     scene, cam, prm, tile, img, r, g, ref, d = cfg1
-    lay = B.htgs_workspace_layout(scene.n, cam, prm, r.launch, r.capacity)
+    tw, th = tile
     n = scene.n
-    rect = workspace_view(r, lay.rect, 2 * n, torch.int32).view(n, 2).cpu().numpy().view(np.uint32)
+    r_rect = Renderer(cam, prm, n, launch=B.c_launch(tile, tile_cover=B.COVER_RECT))
+    img_rect = r_rect.forward(g)
+    lists_rect, rect, lay = _gpu_tile_lists(r_rect, n, cam, prm)
     tx0, tx1 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16
     ty0, ty1 = rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
-    tw, th = tile
     empty = tx0 > tx1
     prect = np.stack([tx0 * tw, (tx1 + 1) * tw - 1, ty0 * th, (ty1 + 1) * th - 1], 1).astype(np.int64)
     prect[:, 1] = np.minimum(prect[:, 1], cam.width - 1)
     prect[:, 3] = np.minimum(prect[:, 3], cam.height - 1)
     prect[empty] = [0, -1, 0, -1]
-    counts, lists = oracle.bin_tiles(prect, cam.width, cam.height, tw, th)
-    ranges = workspace_view(r, lay.ranges, 2 * lay.n_tiles, torch.int32).view(-1, 2).cpu().numpy()
-    total = int(counts.sum())
-    vals = workspace_view(r, lay.sorted_vals, total, torch.int32).cpu().numpy()
-    assert r.last_instances == total
+    counts, olists = oracle.bin_tiles(prect, cam.width, cam.height, tw, th)
+    assert r_rect.last_instances == int(counts.sum())
     off = 0
     for t in range(lay.n_tiles):
         c = int(counts[t])
-        if c:
-            assert ranges[t, 0] == off and ranges[t, 1] == off + c
-        np.testing.assert_array_equal(vals[off:off + c], lists[off:off + c])
+        np.testing.assert_array_equal(lists_rect[t], olists[off:off + c])
         off += c
-    # Validity: the oracle's covered pixel rectangle lies inside the GPU tiles.
+    # Ellipse cover (the render of the fixture): ordered sub-lists.
+    lists, rect_e, _ = _gpu_tile_lists(r, n, cam, prm)
+    np.testing.assert_array_equal(rect_e, rect)
+    assert 0 < r.last_instances <= r_rect.last_instances
+    for t in range(lay.n_tiles):
+        assert np.all(np.diff(lists[t]) > 0)
+        assert np.isin(lists[t], lists_rect[t]).all()
+    assert np.array_equal(img, img_rect.cpu().numpy().astype(np.float64))
+    # Tiles with a pixel clearly inside the cutoff keep the record.
     sp = oracle.preprocess(scene.astype(np.float64), cam, prm)
+    members = [set(map(int, l)) for l in lists]
+    tiles_x = lay.tiles_x
+    needed = 0
     for gi in np.flatnonzero(sp["valid"]):
         x0, x1, y0, y1 = sp["rect"][gi]
         if x0 > x1 or y0 > y1:
@@ -78,6 +100,22 @@ def test_config1_binning_matches_oracle(cfg1):
         assert not empty[gi]
         assert tx0[gi] * tw <= x0 and x1 <= (tx1[gi] + 1) * tw - 1
         assert ty0[gi] * th <= y0 and y1 <= (ty1[gi] + 1) * th - 1
+        rc = float(sp["rho_c"][gi])
+        tiles = set()
+        for y in range(y0, y1 + 1):
+            for x in range(x0, x1 + 1):
+                t = (y // th) * tiles_x + x // tw
+                if t in tiles:
+                    continue
+                hit, rho2, *_ = oracle.eval_pair(sp, int(gi), x + 0.5, y + 0.5)
+                if hit and rho2 <= rc - 4e-6 * max(1.0, rc):
+                    tiles.add(t)
+        for t in tiles:
+            assert int(gi) in members[t], (int(gi), t)
+        needed += len(tiles)
+    print("COVER config1", {"instances_rect": int(r_rect.last_instances), "instances_ellipse": int(r.last_instances),
+                            "tiles_with_inside_pixels": needed})
+    assert needed <= r.last_instances
 
 
 @pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((16, 16), 4), ((32, 16), 1), ((32, 16), 2), ((16, 8), 2),

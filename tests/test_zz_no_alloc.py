@@ -66,7 +66,7 @@ def test_static_scratch_renders_a_scene_just_under_its_ceiling():
     cam = cam.rounded()
     launch = B.c_launch(tile)
     n_max = _static_ceiling(cam, prm, launch)
-    assert 150_000 < n_max < 170_000  # about 208 bytes per Gaussian in 32 MiB
+    assert 130_000 < n_max < 150_000  # about 240 bytes per Gaussian in 32 MiB
     hidden = scenes.small_box_scene(n_max - 2000 - frame.n, seed=5)
     hidden.means[:, 2] = np.float32(-3.0)
     scene = frame.concat(hidden)
