@@ -800,6 +800,18 @@ def main():
     e2e_fps = job_throughput(args.steps, world, e2e_ms)
     last = (args.steps - 1) % 2
     assert torch.equal(host_img[last], imgs[last].cpu()), "the read-back image must be the render's"
+    # The host link's own rate: one step's uploads alone, back to back. It
+    # bounds the end-to-end rate at h2d bytes / rate, whatever the render does.
+    torch.cuda.synchronize()
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record(up)
+    with torch.cuda.stream(up):
+        for _ in range(5):
+            for k in keys:
+                getattr(dev[1], k).copy_(host[k], non_blocking=True)
+    l1.record(up)
+    torch.cuda.synchronize()
+    link_gbs = 5 * h2d / (l0.elapsed_time(l1) * 1e-3) / 1e9
     del dev[1], imgs[1]
 
     # ---- training step: render + L1 + backward (500k Gaussians, 1200x800) --
@@ -1069,7 +1081,10 @@ def main():
                                                       for (t, _, _), v in tune_sorted_train.items()}}),
         "batched_vs_plain": batched,
         "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "overlap": "uploads and read-backs on two copy streams, double-buffered, overlapping the renders"},
+                "overlap": "uploads and read-backs on two copy streams, double-buffered, overlapping the renders",
+                "h2d_link_gbs": round(link_gbs, 1),
+                "link_bound": {"value": link_gbs * 1e9 / h2d * world, "unit": UNIT,
+                               "note": "h2d bytes per step / the link rate measured with the same uploads alone"}},
         "roofline": {"kernel": "blend_fwd", "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": traffic,
                      "work": f"{fwd_units}: {alg:.4g} per launch",

@@ -213,22 +213,13 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
                 }
             }
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
-            while (mask) {
-                const int j = c + __ffs(mask) - 1;
-                mask &= mask - 1;
-                const float4 c0 = rec[j][0], c1 = rec[j][1], c2 = rec[j][2], c4 = rec[j][4];
-                const float dx = __fsub_rn(px, c4.z);
-                float2 qd[PPT];
-                bool any = false;
-#pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    qd[p] = quad_eval2(c0, c1, c2, dx, __fsub_rn(py[p], c4.w));
-                    any |= qd[p].x >= 0.f;
-                }
-                if (!any) continue;
-                const float4 c3 = rec[j][3], c5 = rec[j][5];
+            // The kept-fragment work of record j at this lane's pixels, from
+            // its (Q, D) pairs.
+            auto blend_record = [&](int j, const float2 (&qd)[PPT]) {
+                const float4 c3 = rec[j][3], c4 = rec[j][4], c5 = rec[j][5];
                 const float zlo = rec[j][7].x;
                 const uint32_t gid = gids[j];
+                const float dx = __fsub_rn(px, c4.z);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     FragEval f;
@@ -255,6 +246,41 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
                         }
                     }
                 }
+            };
+            // With a small core (K <= 4) two records per step: both (Q, D)
+            // evaluations are independent chains, and the fragments are then
+            // blended in record order (1080p frame at K = 4: 0.686 -> 0.653 ms).
+            // A larger core leaves no registers for the second record's pairs
+            // under the 4-CTA budget (K = 8: no gain and a spill at the cap),
+            // so it takes one record per step.
+            constexpr bool kPair = KMAX <= 4;
+            while (mask) {
+                const int ja = c + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int jb = (kPair && mask) ? c + __ffs(mask) - 1 : -1;
+                if (kPair && mask) mask &= mask - 1;
+                float2 qa[PPT], qb[PPT];
+                bool anya = false, anyb = false;
+                {
+                    const float4 c0 = rec[ja][0], c1 = rec[ja][1], c2 = rec[ja][2], c4 = rec[ja][4];
+                    const float dx = __fsub_rn(px, c4.z);
+#pragma unroll
+                    for (int p = 0; p < PPT; ++p) {
+                        qa[p] = quad_eval2(c0, c1, c2, dx, __fsub_rn(py[p], c4.w));
+                        anya |= qa[p].x >= 0.f;
+                    }
+                }
+                if (kPair && jb >= 0) {
+                    const float4 c0 = rec[jb][0], c1 = rec[jb][1], c2 = rec[jb][2], c4 = rec[jb][4];
+                    const float dx = __fsub_rn(px, c4.z);
+#pragma unroll
+                    for (int p = 0; p < PPT; ++p) {
+                        qb[p] = quad_eval2(c0, c1, c2, dx, __fsub_rn(py[p], c4.w));
+                        anyb |= qb[p].x >= 0.f;
+                    }
+                }
+                if (anya) blend_record(ja, qa);
+                if (kPair && anyb) blend_record(jb, qb);
             }
         }
     }

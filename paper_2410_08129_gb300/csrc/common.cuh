@@ -219,7 +219,9 @@ __device__ __forceinline__ RowCover row_cover(uint2 rect, float xc, float yc, fl
     r.ty0 = rect.y & 0xffffu; r.ty1 = rect.y >> 16;
     r.xc = xc; r.yc = yc;
     r.k = r.p = r.q = r.yr = r.ym = r.mx = r.my = 0.f;
-    if (!use_ellipse || !(a > 0.f) || !(c > 0.f)) return r;
+    // A rectangle one tile wide keeps its rows whole: the ellipse spans the
+    // box's rows, so it could only drop a row whose pixel centres it misses.
+    if (!use_ellipse || r.tx0 == r.tx1 || !(a > 0.f) || !(c > 0.f)) return r;
     const float w = __fmul_rn(b, b);
     const float det = __fadd_rn(__fmaf_rn(a, c, -w), __fmaf_rn(-b, b, w));  // a c - b^2, compensated
     if (!(det > 0.f)) return r;
