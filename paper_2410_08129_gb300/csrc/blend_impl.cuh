@@ -24,10 +24,17 @@
 
 namespace htgs {
 
+// A staged record takes kStageF4 = 9 float4 slots: the 8 of the record and
+// one holding its id. The 144-byte stride spreads the per-lane cull loads
+// (slot 6 and 7 of 32 consecutive records) over every bank: at a 128-byte
+// stride all of them fall in the same four banks and each quarter-warp load
+// serialises eight ways.
+constexpr int kStageF4 = kRecF4 + 1;
+
 // Dynamic shared memory of the forward: three staging buffers of B records
-// and their ids (B = htgs_launch.smem_batch: 32, 64 or 128).
+// (B = htgs_launch.smem_batch: 32, 64 or 128).
 __host__ __device__ inline size_t fwd_smem_bytes(int B) {
-    return (size_t)3 * B * (kRecF4 * sizeof(float4) + sizeof(uint32_t));
+    return (size_t)3 * B * kStageF4 * sizeof(float4);
 }
 
 // Alpha of one record at a pixel from its (Q, D) pair, evaluated identically
@@ -97,11 +104,11 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     constexpr int TP = TW * TH;
     extern __shared__ float4 s_dyn[];
     const int B = a.tiles.batch;
-    // Whole records in rows of 128 bytes. (Moving the cull words 6 and 7 to
-    // arrays of their own removes the bank conflicts of the per-lane cull
-    // loads but costs registers, and measured 10-15% slower.)
-    float4 *const s_rec = s_dyn;                                      // [3][B][kRecF4]
-    uint32_t *const s_gid = reinterpret_cast<uint32_t *>(s_rec + 3 * B * kRecF4);  // [3][B]
+    // Whole records in rows of kStageF4 float4s, the id in the last one.
+    // (Moving the cull words 6 and 7 to arrays of their own also removes the
+    // bank conflicts of the per-lane cull loads but costs registers, and
+    // measured 10-15% slower.)
+    float4 *const s_rec = s_dyn;  // [3][B][kStageF4]
     __shared__ int s_item;
     __shared__ int s_last;
     if (a.status[kStError] != 0) return;
@@ -168,14 +175,12 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     auto issue = [&](int b) {
         const int nb = batch_size(b);
         const uint32_t base = range.x + (uint32_t)b * B;
-        const int buf = b % 3;
-        float4 *dst = s_rec + (size_t)buf * B * kRecF4;
-        uint32_t *ids = s_gid + buf * B;
+        float4 *dst = s_rec + (size_t)(b % 3) * B * kStageF4;
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
             const uint32_t gid = a.vals[base + j];
-            if (f == 0) ids[j] = gid;
-            cp_async16(dst + k, a.rec + (size_t)gid * kRecF4 + f);
+            if (f == 0) reinterpret_cast<uint32_t *>(dst + j * kStageF4 + kRecF4)[0] = gid;
+            cp_async16(dst + j * kStageF4 + f, a.rec + (size_t)gid * kRecF4 + f);
         }
         cp_async_commit();
     };
@@ -190,8 +195,8 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
         __syncthreads();
         if (b + 2 < nbatches) issue(b + 2);
         const int nb = batch_size(b);
-        const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(s_rec + (size_t)(b % 3) * B * kRecF4);
-        const uint32_t *gids = s_gid + (b % 3) * B;
+        const float4(*rec)[kStageF4] =
+            reinterpret_cast<const float4(*)[kStageF4]>(s_rec + (size_t)(b % 3) * B * kStageF4);
         for (int c = 0; c < nb; c += 32) {
             // Lane c + l tests record c + l against the warp's footprint:
             // its box, then the axis n = A v through the cutoff ellipse
@@ -218,7 +223,7 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
             auto blend_record = [&](int j, const float2 (&qd)[PPT]) {
                 const float4 c3 = rec[j][3], c4 = rec[j][4], c5 = rec[j][5];
                 const float zlo = rec[j][7].x;
-                const uint32_t gid = gids[j];
+                const uint32_t gid = reinterpret_cast<const uint32_t *>(&rec[j][kRecF4])[0];
                 const float dx = __fsub_rn(px, c4.z);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {

@@ -21,11 +21,18 @@ namespace {
 
 constexpr int kSortedBwdBatch = 64;  // records per batch of the adjoint
 
-// Staging shared by both kernels: batch c of the list into buffer c % 3.
+// Shared memory of the sorted forward: three buffers of B staged records
+// (kStageF4 float4 slots each: the record and its id).
+inline size_t sorted_fwd_smem_bytes(int B) {
+    return (size_t)3 * B * kStageF4 * sizeof(float4);
+}
+
+// Staging shared by both kernels: batch c of the list into buffer c % 3,
+// each record in kStageF4 slots with its id in the last (the 144-byte stride
+// keeps the per-lane box loads of the cull free of bank conflicts).
 template <int NT>
 struct Stager {
     float4 *s_rec;
-    uint32_t *s_gid;
     const float4 *rec;
     const uint32_t *vals;
     uint2 range;
@@ -34,13 +41,12 @@ struct Stager {
     __device__ void issue(int c, int tid) const {
         const int nb = size(c);
         const uint32_t base = range.x + (uint32_t)c * B;
-        float4 *dst = s_rec + (size_t)(c % 3) * B * kRecF4;
-        uint32_t *ids = s_gid + (c % 3) * B;
+        float4 *dst = s_rec + (size_t)(c % 3) * B * kStageF4;
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
             const uint32_t gid = vals[base + j];
-            if (f == 0) ids[j] = gid;
-            cp_async16(dst + k, rec + (size_t)gid * kRecF4 + f);
+            if (f == 0) reinterpret_cast<uint32_t *>(dst + j * kStageF4 + kRecF4)[0] = gid;
+            cp_async16(dst + j * kStageF4 + f, rec + (size_t)gid * kRecF4 + f);
         }
         cp_async_commit();
     }
@@ -81,7 +87,7 @@ blend_sorted_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
         uint32_t last = 0;  // list position after the last blended fragment
         bool done = !inside;
 
-        Stager<NT> st{s_dyn, reinterpret_cast<uint32_t *>(s_dyn + 3 * B * kRecF4), a.rec, a.vals,
+        Stager<NT> st{s_dyn, a.rec, a.vals,
                       a.ranges[tile], B};
         const int nbatches = (int)((st.range.y - st.range.x + B - 1) / B);
         if (nbatches > 0) st.issue(0, tid);
@@ -93,7 +99,8 @@ blend_sorted_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
             if (__syncthreads_and(done)) break;
             if (b + 2 < nbatches) st.issue(b + 2, tid);
             const int nb = st.size(b);
-            const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(st.s_rec + (size_t)(b % 3) * B * kRecF4);
+            const float4(*rec)[kStageF4] =
+                reinterpret_cast<const float4(*)[kStageF4]>(st.s_rec + (size_t)(b % 3) * B * kStageF4);
             const uint32_t pos0 = st.range.x + (uint32_t)b * B;
             for (int c = 0; c < nb; c += 32) {
                 bool hit = false;
@@ -149,7 +156,7 @@ blend_sorted_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
 // turn, the records' 16 sums, largest weight, rho_c and id.
 __host__ __device__ inline size_t sorted_bwd_smem_bytes() {
     constexpr int B = kSortedBwdBatch;
-    return (size_t)3 * B * (kRecF4 * sizeof(float4) + sizeof(uint32_t)) + (size_t)2 * B * 19 * sizeof(float);
+    return (size_t)3 * B * kStageF4 * sizeof(float4) + (size_t)2 * B * 19 * sizeof(float);
 }
 
 template <int TW, int TH, bool VIS>
@@ -160,7 +167,7 @@ blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
     constexpr int B = kSortedBwdBatch;
     constexpr float kLn2 = 0.69314718055994531f;
     extern __shared__ float4 s_dyn[];
-    float *s_acc = reinterpret_cast<float *>(s_dyn + 3 * B * kRecF4 + (3 * B + 3) / 4);  // [2][B][19]
+    float *s_acc = reinterpret_cast<float *>(s_dyn + 3 * B * kStageF4);  // [2][B][19]
     __shared__ int s_item;
     if (a.status[kStError] != 0) return;
     const int n_items = min((int)*a.n_items, a.max_items);
@@ -203,7 +210,7 @@ blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
         }
         float T = 1.f;  // S tracks the colour behind the current fragment (S_i after it)
 
-        Stager<NT> st{s_dyn, reinterpret_cast<uint32_t *>(s_dyn + 3 * B * kRecF4), a.rec, a.vals,
+        Stager<NT> st{s_dyn, a.rec, a.vals,
                       a.ranges[tile], B};
         const int nbatches = (int)((st.range.y - st.range.x + B - 1) / B);
         // Accumulators of batch c live in slot c & 1; they are cleared before
@@ -247,8 +254,8 @@ blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
             }
             if (b + 2 < nbatches) st.issue(b + 2, tid);
             const int nb = st.size(b);
-            const float4(*rec)[kRecF4] = reinterpret_cast<const float4(*)[kRecF4]>(st.s_rec + (size_t)(b % 3) * B * kRecF4);
-            const uint32_t *gids = st.s_gid + (b % 3) * B;
+            const float4(*rec)[kStageF4] =
+                reinterpret_cast<const float4(*)[kStageF4]>(st.s_rec + (size_t)(b % 3) * B * kStageF4);
             float *acc_b = s_acc + (b & 1) * B * 19;
             const uint32_t pos0 = st.range.x + (uint32_t)b * B;
             for (int c = 0; c < nb; c += 32) {
@@ -311,7 +318,7 @@ blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
                         if (lane == 0) {
                             if (VIS) atomicMax(reinterpret_cast<int *>(dst + 16), __float_as_int(wmax));
                             dst[17] = c5.w;
-                            dst[18] = __uint_as_float(gids[j]);
+                            dst[18] = rec[j][kRecF4].x;
                         }
                     }
                 }
@@ -326,8 +333,8 @@ blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
 template <int TW, int TH>
 bool run_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const void *fn = (const void *)blend_sorted_fwd_kernel<TW, TH>;
-    const size_t smem = fwd_smem_bytes(a.tiles.batch);
-    if (!allow_dynamic_smem(fn, fwd_smem_bytes(128))) return false;
+    const size_t smem = sorted_fwd_smem_bytes(a.tiles.batch);
+    if (!allow_dynamic_smem(fn, sorted_fwd_smem_bytes(128))) return false;
     const int grid = persistent_grid(fn, TW * TH, smem, a.max_items);
     blend_sorted_fwd_kernel<TW, TH><<<grid, TW * TH, smem, s>>>(b, a);
     return true;

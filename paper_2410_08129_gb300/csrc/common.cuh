@@ -150,6 +150,14 @@ __device__ __forceinline__ float quad_eval(float c0, float c1, float c2, float c
     return __fmaf_rn(y, ty, __fmaf_rn(x, tx, c0));
 }
 
+// Requests the 128-byte lines of [p, p + bytes) into L2 (no register, no
+// completion to wait for), so that a load issued later finds them there.
+__device__ __forceinline__ void prefetch_l2(const void *p, int bytes) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)127;
+    const uintptr_t a1 = reinterpret_cast<uintptr_t>(p) + (uintptr_t)bytes;
+    for (uintptr_t a = a0; a < a1; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // 16-byte asynchronous global -> shared copy (L2 only); completion is
 // awaited with cp_async_wait<N>, which waits for this thread's own copies.
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {

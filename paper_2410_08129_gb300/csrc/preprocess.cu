@@ -356,6 +356,13 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
         const ViewDesc &V = b.v[view_of_record(b, i)];
         const int64_t g = i - V.rec_off;
         const CamArgs &cam = V.cam;
+        // The SH coefficients (most of the bytes read) are used only after the
+        // geometry's chain of dependent steps: ask for them now.
+        if (BAKED && V.baked)
+            prefetch_l2(V.baked + (size_t)g * HTGS_BAKED_FLOATS(V.sh_degree), HTGS_BAKED_FLOATS(V.sh_degree) * 4);
+        else
+            prefetch_l2(V.sh + (size_t)g * 3 * (V.sh_degree + 1) * (V.sh_degree + 1),
+                        12 * (V.sh_degree + 1) * (V.sh_degree + 1));
         Setup S;
         if (BAKED && V.baked)
             setup_geometry_baked(V.baked, HTGS_BAKED_FLOATS(V.sh_degree), g, cam, a.prm, S);
