@@ -200,13 +200,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
     uint32_t *s_k = s_kw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = 1 << a.digit_bits;  // digits of this sort: 2 .. kMaxRadix
-    if (tid == 0) s_ticket = (int)atomicAdd(&a.tickets[pass], 1u);
-    for (int k = tid; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
-    __syncthreads();
-    const int t = s_ticket;
     const uint32_t total = *a.total;
     const uint32_t used = (total + kSortTile - 1) / kSortTile;
-    if ((uint32_t)t >= used) return;
     const int shift = pass * a.digit_bits;
     const uint32_t dmask = (uint32_t)(R - 1);
     const uint32_t *kin = a.keys[src], *vin = a.vals[src];
@@ -241,6 +236,16 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
         __syncthreads();
     };
     block_scan(a.ghist + pass * kMaxRadix, s_scan);
+
+    // Persistent: the block sorts tiles of kSortTile keys in ticket order
+    // until every tile is taken (a tile's look-back waits only on smaller
+    // tickets, which blocks already running hold).
+    for (;;) {
+    if (tid == 0) s_ticket = (int)atomicAdd(&a.tickets[pass], 1u);
+    for (int k = tid; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
+    __syncthreads();
+    const int t = s_ticket;
+    if ((uint32_t)t >= used) break;
 
     // Stable per-warp ranking: item order is (warp, iteration, lane).
     const uint32_t wbase = (uint32_t)t * kSortTile + (uint32_t)warp * 32 * kSortItems;
@@ -355,6 +360,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
             vout[pos] = s_v[i];
         }
     }
+    __syncthreads();  // the next tile reuses the shared arrays
+    } // next tile
 }
 
 // ---------------------------------------------------------------------------
@@ -524,9 +531,15 @@ int launch_sort(const SortArgs &a, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int hist_blocks = std::min<int64_t>((int64_t)sms * 4, (a.capacity + kSortThreads - 1) / kSortThreads + 1);
     histogram_kernel<<<hist_blocks, kSortThreads, 0, s>>>(a);
+    // Enough blocks to fill the GPU; each takes tiles until none is left.
+    static int per_sm = 0;
+    if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kSortThreads, 0) !=
+                            cudaSuccess || per_sm < 1))
+        per_sm = 1;
+    const int grid = std::min<int64_t>(a.n_sort_blocks, (int64_t)sms * per_sm);
     int src = 0;
     for (int p = 0; p < a.passes; ++p) {
-        onesweep_kernel<<<a.n_sort_blocks, kSortThreads, 0, s>>>(a, p, src);
+        onesweep_kernel<<<grid, kSortThreads, 0, s>>>(a, p, src);
         src ^= 1;
     }
     return src;
