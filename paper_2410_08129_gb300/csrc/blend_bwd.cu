@@ -24,6 +24,12 @@ namespace htgs {
 
 constexpr int kBwdThreads = 256;
 
+// A compile-time flag passed to the record walk (one instance per case).
+template <bool V>
+struct Flag {
+    static constexpr bool value = V;
+};
+
 // frag_alpha without the early exit: every field is computed, and the result
 // says whether the fragment is kept (for a kept one the fields equal those of
 // frag_alpha bit for bit; for the others they are unused).
@@ -206,6 +212,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
         cp_async_commit();
     };
     constexpr float kLn2 = 0.69314718055994531f;
+    const float rc_clamp = 2.f * logf(alpha_max / tau_alpha) - 1e-3f;
     uint32_t j = grab();
     int slot = 0;
     if (j < range.y) issue(j, 0);
@@ -229,6 +236,9 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             const float4 c0 = rec[0], c1 = rec[1], c2 = rec[2], c4 = rec[4], c5 = rec[5];
             const float zlo = rec[7].x;
             const bool may_core = K > 0 && (tile_open || !(zlo > tile_zmax));
+            // alpha reaches its clamp only where o >= alpha_max, i.e. rho_c >=
+            // 2 ln(alpha_max / tau_alpha) (less a margin for rounding).
+            const bool may_clamp = c5.w >= rc_clamp;
             float2 acc[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -236,91 +246,106 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             float wmax = 0.f;  // largest blending weight of the record in this tile
             bool touched = false;
             const int lx = lane & 7, ly = lane >> 3;
-            // The adjoint of one kept fragment at pixel p (offset dx, dy).
-            auto fragment = [&](float dx, float dy, int p, const FragEval &f) {
-                const float al = f.alpha;
-                bool in_core = false;
-                if (may_core && al >= tau_K) {
-                    const float2 PC = s_pc[p];
-                    if (PC.x == INFINITY) {
-                        in_core = true;
-                    } else if (!(zlo > PC.x)) {
-                        // (depths of this splat are >= zlo, so zlo > last
-                        // core depth means the fragment is not in the core)
-                        const float z = frag_depth(rec[3], c4, dx, dy, f.rD);
-                        in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
+            // The walk over the record's box, compiled for each case of the
+            // two record-wide conditions: whether a fragment can belong to a
+            // core of this tile (most records of a deep tile cannot), and
+            // whether its alpha can reach the clamp.
+            auto walk = [&](auto core_flag, auto clamp_flag) {
+                constexpr bool CORE = decltype(core_flag)::value;
+                constexpr bool CLAMP = decltype(clamp_flag)::value;
+                // The adjoint of one kept fragment at pixel p (offset dx, dy).
+                auto fragment = [&](float dx, float dy, int p, const FragEval &f) {
+                    const float al = f.alpha;
+                    bool in_core = false;
+                    if (CORE && al >= tau_K) {
+                        const float2 PC = s_pc[p];
+                        if (PC.x == INFINITY) {
+                            in_core = true;
+                        } else if (!(zlo > PC.x)) {
+                            // (depths of this splat are >= zlo, so zlo > last
+                            // core depth means the fragment is not in the core)
+                            const float z = frag_depth(rec[3], c4, dx, dy, f.rD);
+                            in_core = z < PC.x || (z == PC.x && gid <= __float_as_uint(PC.y));
+                        }
+                    }
+                    if (NOTAIL && !in_core) return;  // an omitted tail has no gradient
+                    float dA;
+                    if (in_core) {
+                        const float4 PA = s_pa[p];
+                        float w = 0.f, s = 0.f;
+                        for (int r = 0; r < K; ++r)
+                            if (s_cg[(size_t)r * TP + p] == gid) {
+                                w = s_cw[(size_t)r * TP + p];
+                                s = s_cv[(size_t)r * TP + p];
+                                break;
+                            }
+                        dA = w;
+                        gc0 = __fmaf_rn(PA.x, s, gc0);
+                        gc1 = __fmaf_rn(PA.y, s, gc1);
+                        gc2 = __fmaf_rn(PA.z, s, gc2);
+                        if (VIS) wmax = fmaxf(wmax, s);
+                    } else {
+                        const float4 PB = s_pb[p];
+                        const float k0 = s_pa[p].w;
+                        const float inv = rcp_approx(1.f - al);
+                        dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + k0 + PB.w * inv;
+                        gc0 = __fmaf_rn(PB.x, al, gc0);
+                        gc1 = __fmaf_rn(PB.y, al, gc1);
+                        gc2 = __fmaf_rn(PB.z, al, gc2);
+                        if (VIS) wmax = fmaxf(wmax, al * s_wt[p]);
+                    }
+                    touched = true;
+                    // With g = alpha dL/dalpha: dL/drho^2 = -g/2, and as
+                    // rho^2 = N / D = rho_c - 2 ln2 t, dL/dN = -e/2 and
+                    // dL/dD = e rho^2 / 2 = (rho_c e - 2 ln2 e t) / 2 for
+                    // e = g / D. The pixel adds the moments of (e, e t); the
+                    // (record, tile) sums become dL/dN and dL/dD once, after
+                    // the warp reduction. A clamped alpha (araw >= alpha_max)
+                    // passes no gradient to the geometry: g = 0 adds nothing.
+                    const float g = (!CLAMP || f.araw < alpha_max) ? dA * al : 0.f;
+                    gaa += g;
+                    const float e = g * f.rD;
+                    const float2 et = make_float2(e, e * f.t);
+                    const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
+                    const float2 ex = fmul2(et, X), ey = fmul2(et, Y);
+                    acc[0] = fadd2(acc[0], et);
+                    acc[1] = fadd2(acc[1], ex);
+                    acc[2] = fadd2(acc[2], ey);
+                    acc[3] = ffma2(ex, X, acc[3]);
+                    acc[4] = ffma2(ex, Y, acc[4]);
+                    acc[5] = ffma2(ey, Y, acc[5]);
+                };
+                // Pixel centres are integers plus 1/2, exact in FP32, so
+                // stepping them by whole pixels gives (float)x + 0.5 bit for
+                // bit. Two pixels of a row are evaluated together (the cutoff
+                // test and alpha for both before either's adjoint), which
+                // gives the scheduler two independent chains; each lane still
+                // visits its pixels in row order.
+                const float pxl = (float)(ix0 + lx) + 0.5f;
+                for (int y = iy0 + ly; y <= iy1; y += 4) {
+                    const float dy = __fsub_rn((float)y + 0.5f, c4.w);
+                    const int prow = (y - y0) * TW - x0 + ix0 + lx;
+#pragma unroll
+                    for (int q = 0; q < TW / 8; q += 2) {
+                        const bool in0 = ix0 + lx + 8 * q <= ix1;
+                        const bool in1 = q + 1 < TW / 8 && ix0 + lx + 8 * (q + 1) <= ix1;
+                        const float dx0 = __fsub_rn(pxl + 8.f * q, c4.z);
+                        const float dx1 = __fsub_rn(pxl + 8.f * (q + 1), c4.z);
+                        FragEval f0, f1;
+                        const bool k0 = frag_alpha_all(quad_eval2(c0, c1, c2, dx0, dy), tau_alpha, alpha_max, f0) && in0;
+                        const bool k1 = frag_alpha_all(quad_eval2(c0, c1, c2, dx1, dy), tau_alpha, alpha_max, f1) && in1;
+                        if (k0) fragment(dx0, dy, prow + 8 * q, f0);
+                        if (k1) fragment(dx1, dy, prow + 8 * (q + 1), f1);
+                        if (!in1) break;
                     }
                 }
-                if (NOTAIL && !in_core) return;  // an omitted tail has no gradient
-                float dA;
-                if (in_core) {
-                    const float4 PA = s_pa[p];
-                    float w = 0.f, s = 0.f;
-                    for (int r = 0; r < K; ++r)
-                        if (s_cg[(size_t)r * TP + p] == gid) {
-                            w = s_cw[(size_t)r * TP + p];
-                            s = s_cv[(size_t)r * TP + p];
-                            break;
-                        }
-                    dA = w;
-                    gc0 = __fmaf_rn(PA.x, s, gc0);
-                    gc1 = __fmaf_rn(PA.y, s, gc1);
-                    gc2 = __fmaf_rn(PA.z, s, gc2);
-                    if (VIS) wmax = fmaxf(wmax, s);
-                } else {
-                    const float4 PB = s_pb[p];
-                    const float k0 = s_pa[p].w;
-                    const float inv = rcp_approx(1.f - al);
-                    dA = PB.x * c5.x + PB.y * c5.y + PB.z * c5.z + k0 + PB.w * inv;
-                    gc0 = __fmaf_rn(PB.x, al, gc0);
-                    gc1 = __fmaf_rn(PB.y, al, gc1);
-                    gc2 = __fmaf_rn(PB.z, al, gc2);
-                    if (VIS) wmax = fmaxf(wmax, al * s_wt[p]);
-                }
-                touched = true;
-                // With g = alpha dL/dalpha: dL/drho^2 = -g/2, and as
-                // rho^2 = N / D = rho_c - 2 ln2 t, dL/dN = -e/2 and
-                // dL/dD = e rho^2 / 2 = (rho_c e - 2 ln2 e t) / 2 for
-                // e = g / D. The pixel adds the moments of (e, e t); the
-                // (record, tile) sums become dL/dN and dL/dD once, after
-                // the warp reduction. A clamped alpha (araw >= alpha_max)
-                // passes no gradient to the geometry: g = 0 adds nothing.
-                const float g = f.araw < alpha_max ? dA * al : 0.f;
-                gaa += g;
-                const float e = g * f.rD;
-                const float2 et = make_float2(e, e * f.t);
-                const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
-                const float2 ex = fmul2(et, X), ey = fmul2(et, Y);
-                acc[0] = fadd2(acc[0], et);
-                acc[1] = fadd2(acc[1], ex);
-                acc[2] = fadd2(acc[2], ey);
-                acc[3] = ffma2(ex, X, acc[3]);
-                acc[4] = ffma2(ex, Y, acc[4]);
-                acc[5] = ffma2(ey, Y, acc[5]);
             };
-            // Pixel centres are integers plus 1/2, exact in FP32, so stepping
-            // them by whole pixels gives (float)x + 0.5 bit for bit. Two
-            // pixels of a row are evaluated together (the cutoff test and
-            // alpha for both before either's adjoint), which gives the
-            // scheduler two independent chains; each lane still visits its
-            // pixels in row order.
-            const float pxl = (float)(ix0 + lx) + 0.5f;
-            for (int y = iy0 + ly; y <= iy1; y += 4) {
-                const float dy = __fsub_rn((float)y + 0.5f, c4.w);
-                const int prow = (y - y0) * TW - x0 + ix0 + lx;
-#pragma unroll
-                for (int q = 0; q < TW / 8; q += 2) {
-                    const bool in0 = ix0 + lx + 8 * q <= ix1;
-                    const bool in1 = q + 1 < TW / 8 && ix0 + lx + 8 * (q + 1) <= ix1;
-                    const float dx0 = __fsub_rn(pxl + 8.f * q, c4.z);
-                    const float dx1 = __fsub_rn(pxl + 8.f * (q + 1), c4.z);
-                    FragEval f0, f1;
-                    const bool k0 = frag_alpha_all(quad_eval2(c0, c1, c2, dx0, dy), tau_alpha, alpha_max, f0) && in0;
-                    const bool k1 = frag_alpha_all(quad_eval2(c0, c1, c2, dx1, dy), tau_alpha, alpha_max, f1) && in1;
-                    if (k0) fragment(dx0, dy, prow + 8 * q, f0);
-                    if (k1) fragment(dx1, dy, prow + 8 * (q + 1), f1);
-                    if (!in1) break;
-                }
+            if (may_core) {
+                if (may_clamp) walk(Flag<true>{}, Flag<true>{});
+                else walk(Flag<true>{}, Flag<false>{});
+            } else {
+                if (may_clamp) walk(Flag<false>{}, Flag<true>{});
+                else walk(Flag<false>{}, Flag<false>{});
             }
             if (VIS) {
                 for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
