@@ -32,13 +32,16 @@ struct Flag {
 
 // frag_alpha without the early exit: every field is computed, and the result
 // says whether the fragment is kept (for a kept one the fields equal those of
-// frag_alpha bit for bit; for the others they are unused).
+// frag_alpha bit for bit; for the others they are unused). CLAMP = false is
+// for records whose alpha cannot reach alpha_max (there the clamp is the
+// identity).
+template <bool CLAMP = true>
 __device__ __forceinline__ bool frag_alpha_all(float2 qd, float tau_alpha, float alpha_max, FragEval &f) {
     f.D = qd.y;
     f.rD = rcp_approx(f.D);
     f.t = __fmul_rn(qd.x, f.rD);
     f.araw = __fmul_rn(tau_alpha, ex2_approx(f.t));
-    f.alpha = fminf(f.araw, alpha_max);
+    f.alpha = CLAMP ? fminf(f.araw, alpha_max) : f.araw;
     return qd.x >= 0.f && qd.y > 0.f;
 }
 
@@ -250,9 +253,10 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             // two record-wide conditions: whether a fragment can belong to a
             // core of this tile (most records of a deep tile cannot), and
             // whether its alpha can reach the clamp.
-            auto walk = [&](auto core_flag, auto clamp_flag) {
+            auto walk = [&](auto core_flag, auto clamp_flag, auto full_flag) {
                 constexpr bool CORE = decltype(core_flag)::value;
                 constexpr bool CLAMP = decltype(clamp_flag)::value;
+                constexpr bool FULL = decltype(full_flag)::value;  // the box spans the tile's columns
                 // The adjoint of one kept fragment at pixel p (offset dx, dy).
                 auto fragment = [&](float dx, float dy, int p, const FragEval &f) {
                     const float al = f.alpha;
@@ -327,25 +331,31 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                     const int prow = (y - y0) * TW - x0 + ix0 + lx;
 #pragma unroll
                     for (int q = 0; q < TW / 8; q += 2) {
-                        const bool in0 = ix0 + lx + 8 * q <= ix1;
-                        const bool in1 = q + 1 < TW / 8 && ix0 + lx + 8 * (q + 1) <= ix1;
+                        const bool in0 = FULL || ix0 + lx + 8 * q <= ix1;
+                        const bool in1 = q + 1 < TW / 8 && (FULL || ix0 + lx + 8 * (q + 1) <= ix1);
                         const float dx0 = __fsub_rn(pxl + 8.f * q, c4.z);
                         const float dx1 = __fsub_rn(pxl + 8.f * (q + 1), c4.z);
                         FragEval f0, f1;
-                        const bool k0 = frag_alpha_all(quad_eval2(c0, c1, c2, dx0, dy), tau_alpha, alpha_max, f0) && in0;
-                        const bool k1 = frag_alpha_all(quad_eval2(c0, c1, c2, dx1, dy), tau_alpha, alpha_max, f1) && in1;
+                        const bool k0 =
+                            frag_alpha_all<CLAMP>(quad_eval2(c0, c1, c2, dx0, dy), tau_alpha, alpha_max, f0) && in0;
+                        const bool k1 =
+                            frag_alpha_all<CLAMP>(quad_eval2(c0, c1, c2, dx1, dy), tau_alpha, alpha_max, f1) && in1;
                         if (k0) fragment(dx0, dy, prow + 8 * q, f0);
                         if (k1) fragment(dx1, dy, prow + 8 * (q + 1), f1);
                         if (!in1) break;
                     }
                 }
             };
+            const bool full = ix0 == x0 && ix1 == x0 + TW - 1;
             if (may_core) {
-                if (may_clamp) walk(Flag<true>{}, Flag<true>{});
-                else walk(Flag<true>{}, Flag<false>{});
+                if (may_clamp) walk(Flag<true>{}, Flag<true>{}, Flag<false>{});
+                else walk(Flag<true>{}, Flag<false>{}, Flag<false>{});
+            } else if (may_clamp) {
+                walk(Flag<false>{}, Flag<true>{}, Flag<false>{});
+            } else if (full) {
+                walk(Flag<false>{}, Flag<false>{}, Flag<true>{});
             } else {
-                if (may_clamp) walk(Flag<false>{}, Flag<true>{});
-                else walk(Flag<false>{}, Flag<false>{});
+                walk(Flag<false>{}, Flag<false>{}, Flag<false>{});
             }
             if (VIS) {
                 for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
