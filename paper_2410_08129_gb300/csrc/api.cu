@@ -269,9 +269,45 @@ void make_batch(int n_views, const htgs_view *views, const Layout &L, bool backw
     }
 }
 
+// The kernels of one call are launched as programmatic dependents of their
+// predecessors, unless the caller asked for timing events between the phases
+// (an event recorded between two dependent kernels would not mark the
+// boundary between them).
+struct DependentLaunchScope {
+    explicit DependentLaunchScope(const htgs_launch *launch) {
+        bool events = false;
+        if (launch)
+            for (int i = 0; i < 6; ++i) events |= launch->events[i] != nullptr;
+        set_dependent_launch(!events);
+    }
+    ~DependentLaunchScope() { set_dependent_launch(false); }
+};
+
+htgs_status render_batch_impl(int n_views, const htgs_view *views, const htgs_params *params,
+                              const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                              int64_t capacity, void *stream);
+htgs_status render_batch_backward_impl(int n_views, const htgs_view *views, const htgs_params *params,
+                                       const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                                       int64_t capacity, void *stream);
+
 htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params *params,
                          const htgs_launch *launch, void *workspace, size_t workspace_bytes,
                          int64_t capacity, void *stream) {
+    DependentLaunchScope scope(launch);
+    return render_batch_impl(n_views, views, params, launch, workspace, workspace_bytes, capacity, stream);
+}
+
+htgs_status render_batch_backward(int n_views, const htgs_view *views, const htgs_params *params,
+                                  const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                                  int64_t capacity, void *stream) {
+    DependentLaunchScope scope(launch);
+    return render_batch_backward_impl(n_views, views, params, launch, workspace, workspace_bytes, capacity,
+                                      stream);
+}
+
+htgs_status render_batch_impl(int n_views, const htgs_view *views, const htgs_params *params,
+                              const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                              int64_t capacity, void *stream) {
     HostView hv[kMaxViews];
     htgs_status st = collect(n_views, views, hv);
     if (st) return st;
@@ -413,9 +449,9 @@ htgs_status render_batch(int n_views, const htgs_view *views, const htgs_params 
     return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;
 }
 
-htgs_status render_batch_backward(int n_views, const htgs_view *views, const htgs_params *params,
-                                  const htgs_launch *launch, void *workspace, size_t workspace_bytes,
-                                  int64_t capacity, void *stream) {
+htgs_status render_batch_backward_impl(int n_views, const htgs_view *views, const htgs_params *params,
+                                       const htgs_launch *launch, void *workspace, size_t workspace_bytes,
+                                       int64_t capacity, void *stream) {
     HostView hv[kMaxViews];
     htgs_status st = collect(n_views, views, hv, true);
     if (st) return st;
@@ -492,7 +528,7 @@ htgs_status render_batch_backward(int n_views, const htgs_view *views, const htg
         pb.acc = acc;
         pb.vis = bb.vis;
         pb.accumulate = accumulate ? 1 : 0;
-        preprocess_backward_kernel<<<L.n_blocks, kPreThreads, 0, s>>>(b, pb);
+        launch_k(preprocess_backward_kernel, L.n_blocks, kPreThreads, 0, s, b, pb);
     }
     mark(launch, 3, s);
     return cudaGetLastError() == cudaSuccess ? HTGS_OK : HTGS_ERR_CUDA;

@@ -48,6 +48,7 @@ __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long 
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(BinArgs a) {
+    dependent_entry();
     __shared__ uint64_t warp_tot[kScanThreads / 32];
     const int nb = a.n_blocks;
     const int per = (nb + kScanThreads - 1) / kScanThreads;
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(BinArgs a) {
 // Emit: the instances of a Gaussian are its cover's tiles, row by row.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant__ Batch b, BinArgs a) {
+    dependent_entry();
     __shared__ uint32_t warp_tot[kPreThreads / 32];
     if (a.status[kStError] == HTGS_ERR_OVERFLOW) return;
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(kPreThreads) emit_kernel(const __grid_constant
 // Radix sort: digit histograms for all passes in one read.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) histogram_kernel(SortArgs a) {
+    dependent_entry();
     __shared__ uint32_t h[kMaxPasses * kMaxRadix];
     const int R = 1 << a.digit_bits;
     for (int k = threadIdx.x; k < a.passes * kMaxRadix; k += kSortThreads) h[k] = 0;
@@ -186,6 +189,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int pass, int src) {
+    dependent_entry();
     // s_whist (per-warp digit counts, then their prefixes) and s_k (the block's
     // keys in digit order) are alive at different times and share storage.
     __shared__ uint32_t s_kw[kSortTile > kSortWarps * kMaxRadix ? kSortTile : kSortWarps * kMaxRadix];
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
 // Tile ranges from the sorted keys.
 // ---------------------------------------------------------------------------
 __global__ void ranges_kernel(RangeArgs a) {
+    dependent_entry();
     const uint32_t total = *a.total;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const uint32_t t = a.keys[i];
@@ -389,6 +394,7 @@ __device__ __forceinline__ int length_bucket(uint32_t len) {
 }
 
 __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a) {
+    dependent_entry();
     __shared__ uint32_t s_cnt[kSchedBuckets];
     __shared__ uint32_t s_pos[kSchedBuckets];
     __shared__ uint32_t s_slots;
@@ -487,6 +493,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a)
 __global__ void __launch_bounds__(kPreThreads) permute_counts_kernel(long long n, const uint32_t *perm,
                                                                      const uint32_t *count, uint32_t *count_p,
                                                                      uint32_t *block_sums) {
+    dependent_entry();
     __shared__ uint32_t warp_sums[kPreThreads / 32];
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     uint32_t c = 0;
@@ -510,19 +517,19 @@ __global__ void __launch_bounds__(kPreThreads) permute_counts_kernel(long long n
 void launch_permute_counts(long long n, const uint32_t *perm, const uint32_t *count, uint32_t *count_p,
                            uint32_t *block_sums, cudaStream_t s) {
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
-    if (blocks > 0) permute_counts_kernel<<<blocks, kPreThreads, 0, s>>>(n, perm, count, count_p, block_sums);
+    if (blocks > 0) launch_k(permute_counts_kernel, blocks, kPreThreads, 0, s, n, perm, count, count_p, block_sums);
 }
 
 void launch_schedule(const ScheduleArgs &a, cudaStream_t s) {
-    schedule_kernel<<<1, kSchedThreads, 0, s>>>(a);
+    launch_k(schedule_kernel, 1, kSchedThreads, 0, s, a);
 }
 
 void launch_scan_blocks(const BinArgs &a, cudaStream_t s) {
-    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(a);
+    launch_k(scan_blocks_kernel, 1, kScanThreads, 0, s, a);
 }
 
 void launch_emit(const Batch &b, const BinArgs &a, cudaStream_t s) {
-    if (a.n_blocks > 0) emit_kernel<<<a.n_blocks, kPreThreads, 0, s>>>(b, a);
+    if (a.n_blocks > 0) launch_k(emit_kernel, a.n_blocks, kPreThreads, 0, s, b, a);
 }
 
 int launch_sort(const SortArgs &a, cudaStream_t s) {
@@ -530,7 +537,7 @@ int launch_sort(const SortArgs &a, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int hist_blocks = std::min<int64_t>((int64_t)sms * 4, (a.capacity + kSortThreads - 1) / kSortThreads + 1);
-    histogram_kernel<<<hist_blocks, kSortThreads, 0, s>>>(a);
+    launch_k(histogram_kernel, hist_blocks, kSortThreads, 0, s, a);
     // Enough blocks to fill the GPU; each takes tiles until none is left.
     static int per_sm = 0;
     if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kSortThreads, 0) !=
@@ -539,7 +546,7 @@ int launch_sort(const SortArgs &a, cudaStream_t s) {
     const int grid = std::min<int64_t>(a.n_sort_blocks, (int64_t)sms * per_sm);
     int src = 0;
     for (int p = 0; p < a.passes; ++p) {
-        onesweep_kernel<<<grid, kSortThreads, 0, s>>>(a, p, src);
+        launch_k(onesweep_kernel, grid, kSortThreads, 0, s, a, p, src);
         src ^= 1;
     }
     return src;
@@ -549,8 +556,15 @@ void launch_ranges(RangeArgs a, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    ranges_kernel<<<sms * 8, 256, 0, s>>>(a);
+    launch_k(ranges_kernel, sms * 8, 256, 0, s, a);
 }
+
+namespace {
+thread_local bool t_dependent_launch = false;
+}
+
+void set_dependent_launch(bool on) { t_dependent_launch = on; }
+bool dependent_launch() { return t_dependent_launch; }
 
 bool allow_dynamic_smem(const void *kernel, size_t bytes) {
     // Once per (kernel, device): the attribute persists, and repeating the

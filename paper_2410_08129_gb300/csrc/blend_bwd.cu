@@ -52,6 +52,7 @@ __host__ __device__ inline size_t bwd_smem_bytes(int TP, int K) {
 
 template <int TW, int TH, bool NOTAIL, bool VIS>
 __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
+    dependent_entry();
     constexpr int TP = TW * TH;
     constexpr int NW = kBwdThreads / 32;
     extern __shared__ float4 smem[];
@@ -393,7 +394,7 @@ bool run_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     const void *fn = (const void *)blend_bwd_kernel<TW, TH, NOTAIL, VIS>;
     if (!allow_dynamic_smem(fn, bwd_smem_bytes(TW * TH, HTGS_MAX_K))) return false;
     const int grid = persistent_grid(fn, kBwdThreads, smem, a.max_items);
-    blend_bwd_kernel<TW, TH, NOTAIL, VIS><<<grid, kBwdThreads, smem, s>>>(b, a);
+    launch_k(blend_bwd_kernel<TW, TH, NOTAIL, VIS>, grid, kBwdThreads, smem, s, b, a);
     return true;
 }
 

@@ -97,6 +97,7 @@ constexpr int fwd_min_blocks() {
 template <int KMAX, int TW, int TH, int PPT, bool NOTAIL>
 __global__ void __launch_bounds__(TW *TH / PPT, fwd_min_blocks<KMAX, PPT, TW * TH / PPT>())
 blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
+    dependent_entry();
     constexpr int NT = TW * TH / PPT;
     constexpr int WY = 4 * PPT;  // warp footprint: 8 x WY pixels
     constexpr int WPR = TW / 8;  // footprints per tile row
@@ -441,7 +442,7 @@ bool run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const size_t smem = fwd_smem_bytes(a.tiles.batch);
     if (!allow_dynamic_smem(fn, fwd_smem_bytes(128))) return false;
     const int grid = persistent_grid(fn, NT, smem, a.max_items);
-    blend_fwd_kernel<KMAX, TW, TH, PPT, NOTAIL><<<grid, NT, smem, s>>>(b, a);
+    launch_k(blend_fwd_kernel<KMAX, TW, TH, PPT, NOTAIL>, grid, NT, smem, s, b, a);
     return true;
 }
 

@@ -55,6 +55,7 @@ struct Stager {
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH, 1024 / (TW * TH))
 blend_sorted_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
+    dependent_entry();
     constexpr int NT = TW * TH;
     constexpr int WPR = TW / 8;
     extern __shared__ float4 s_dyn[];
@@ -162,6 +163,7 @@ __host__ __device__ inline size_t sorted_bwd_smem_bytes() {
 template <int TW, int TH, bool VIS>
 __global__ void __launch_bounds__(TW *TH, 768 / (TW * TH) > 0 ? 768 / (TW * TH) : 1)
 blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
+    dependent_entry();
     constexpr int NT = TW * TH;
     constexpr int WPR = TW / 8;
     constexpr int B = kSortedBwdBatch;
@@ -336,7 +338,7 @@ bool run_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const size_t smem = sorted_fwd_smem_bytes(a.tiles.batch);
     if (!allow_dynamic_smem(fn, sorted_fwd_smem_bytes(128))) return false;
     const int grid = persistent_grid(fn, TW * TH, smem, a.max_items);
-    blend_sorted_fwd_kernel<TW, TH><<<grid, TW * TH, smem, s>>>(b, a);
+    launch_k(blend_sorted_fwd_kernel<TW, TH>, grid, TW * TH, smem, s, b, a);
     return true;
 }
 
@@ -346,7 +348,7 @@ bool run_sorted_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s) {
     const size_t smem = sorted_bwd_smem_bytes();
     if (!allow_dynamic_smem(fn, smem)) return false;
     const int grid = persistent_grid(fn, TW * TH, smem, a.max_items);
-    blend_sorted_bwd_kernel<TW, TH, VIS><<<grid, TW * TH, smem, s>>>(b, a);
+    launch_k(blend_sorted_bwd_kernel<TW, TH, VIS>, grid, TW * TH, smem, s, b, a);
     return true;
 }
 

@@ -150,6 +150,15 @@ __device__ __forceinline__ float quad_eval(float c0, float c1, float c2, float c
     return __fmaf_rn(y, ty, __fmaf_rn(x, tx, c0));
 }
 
+// First statement of every kernel: waits until the previous kernel of the
+// stream has completed and its writes are visible (a no-op unless this
+// kernel was launched as a programmatic dependent), then lets the next
+// kernel's launch begin.
+__device__ __forceinline__ void dependent_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Requests the 128-byte lines of [p, p + bytes) into L2 (no register, no
 // completion to wait for), so that a load issued later finds them there.
 __device__ __forceinline__ void prefetch_l2(const void *p, int bytes) {

@@ -272,6 +272,35 @@ bool launch_blend_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s);
 bool launch_blend_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s);
 bool launch_blend_sorted_bwd(const Batch &b, const BlendBwdArgs &a, cudaStream_t s);
 
+// Programmatic dependent launch for the kernels of one render call: while
+// it is on (set_dependent_launch, per host thread), launch_k starts each
+// kernel with cudaLaunchAttributeProgrammaticStreamSerialization, so that
+// its CTAs may become resident while the previous kernel's last CTAs run;
+// every kernel begins with dependent_entry(), which waits for the previous
+// kernel to complete before touching memory. Off, launch_k is a plain launch.
+void set_dependent_launch(bool on);
+bool dependent_launch();
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+    if (!dependent_launch()) {
+        kernel<<<grid, block, smem, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // CTAs per SM the persistent kernels are launched with (occupancy query).
 int persistent_grid(const void *kernel, int threads, size_t dyn_smem, int items);
 // Raises a kernel's dynamic shared-memory limit to `bytes` (once per device).

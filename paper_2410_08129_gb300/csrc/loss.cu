@@ -12,6 +12,7 @@ __global__ void __launch_bounds__(kLossThreads)
 l1_kernel(const float4 *__restrict__ img, const float4 *__restrict__ tgt, int64_t n4,
           const float *__restrict__ img_s, const float *__restrict__ tgt_s, int64_t n, float inv_n,
           float4 *__restrict__ dl, float *__restrict__ dl_s, float *loss) {
+    dependent_entry();
     float acc = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * kLossThreads + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * kLossThreads) {

@@ -319,6 +319,7 @@ __device__ void cutoff_ellipse(const float (&q)[6], float (&A)[3]) {
 // the layout setup_geometry_baked reads: [q / |q|][mean, 2 ln o][s, 0][SH..].
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads) bake_kernel(BakeArgs a) {
+    dependent_entry();
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     if (i >= a.n) return;
     Setup S;
@@ -343,6 +344,7 @@ __global__ void __launch_bounds__(kPreThreads) bake_kernel(BakeArgs a) {
 template <bool BAKED>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
+    dependent_entry();
     __shared__ float4 s_recs[kPreThreads / 32][32 * kRecF4];
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     uint32_t count = 0;
@@ -556,6 +558,7 @@ preprocess_kernel(const __grid_constant__ Batch b, PreArgs a) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
+    dependent_entry();
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
     if (i >= b.n_rec) return;
     // Record i is Gaussian g of the scene that view v renders.
@@ -700,9 +703,9 @@ preprocess_backward_kernel(const __grid_constant__ Batch b, PreBwdArgs a) {
 
 void launch_preprocess(bool any_baked, int blocks, const Batch &b, const PreArgs &a, cudaStream_t s) {
     if (any_baked)
-        preprocess_kernel<true><<<blocks, kPreThreads, 0, s>>>(b, a);
+        launch_k(preprocess_kernel<true>, blocks, kPreThreads, 0, s, b, a);
     else
-        preprocess_kernel<false><<<blocks, kPreThreads, 0, s>>>(b, a);
+        launch_k(preprocess_kernel<false>, blocks, kPreThreads, 0, s, b, a);
 }
 
 } // namespace htgs

@@ -127,6 +127,7 @@ __device__ __forceinline__ Band band_of(const CsArgs &a, int s) {
 }
 
 __global__ void __launch_bounds__(kCsThreads) cs_count_kernel(CsArgs a) {
+    dependent_entry();
     __shared__ uint32_t s_hist[kCsBandTiles];
     const Band B = band_of(a, blockIdx.y);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_count_kernel(CsArgs a) {
 constexpr int kColGroups = 8;
 
 __global__ void __launch_bounds__(32 * kColGroups) cs_colscan_kernel(CsArgs a) {
+    dependent_entry();
     __shared__ uint32_t s_part[kColGroups][32];
     const int T = a.n_tiles, nb = a.nb;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(32 * kColGroups) cs_colscan_kernel(CsArgs a) {
 }
 
 __global__ void __launch_bounds__(kCsThreads) cs_emit_kernel(CsArgs a) {
+    dependent_entry();
     // s_base[t]: global position of this block's first instance of band tile t.
     // s_wc[h][t]: 16-bit counters of warps 2h (low half) and 2h + 1 (high
     // half): first the warp's count of tile t, then its running position
@@ -257,15 +260,15 @@ bool cs_plan(int n_views, int tiles_x, int tiles_y, long long n, CsPlan &p) {
 }
 
 void launch_cs_count(const CsArgs &a, cudaStream_t s) {
-    if (a.nb > 0) cs_count_kernel<<<dim3(a.nb, a.n_bands), kCsThreads, 0, s>>>(a);
+    if (a.nb > 0) launch_k(cs_count_kernel, dim3(a.nb, a.n_bands), kCsThreads, 0, s, a);
 }
 
 void launch_cs_colscan(const CsArgs &a, cudaStream_t s) {
-    cs_colscan_kernel<<<(a.n_tiles + 31) / 32, 32 * kColGroups, 0, s>>>(a);
+    launch_k(cs_colscan_kernel, (a.n_tiles + 31) / 32, 32 * kColGroups, 0, s, a);
 }
 
 void launch_cs_emit(const CsArgs &a, cudaStream_t s) {
-    if (a.nb > 0) cs_emit_kernel<<<dim3(a.nb, a.n_bands), kCsThreads, 0, s>>>(a);
+    if (a.nb > 0) launch_k(cs_emit_kernel, dim3(a.nb, a.n_bands), kCsThreads, 0, s, a);
 }
 
 }  // namespace htgs
