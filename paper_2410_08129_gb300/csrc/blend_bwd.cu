@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             auto walk = [&](auto core_flag, auto clamp_flag, auto full_flag) {
                 constexpr bool CORE = decltype(core_flag)::value;
                 constexpr bool CLAMP = decltype(clamp_flag)::value;
-                constexpr bool FULL = decltype(full_flag)::value;  // the box spans the tile's columns
+                constexpr bool FULL = decltype(full_flag)::value;  // the box spans the whole tile
                 // The adjoint of one kept fragment at pixel p (offset dx, dy).
                 auto fragment = [&](float dx, float dy, int p, const FragEval &f) {
                     const float al = f.alpha;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                 // gives the scheduler two independent chains; each lane still
                 // visits its pixels in row order.
                 const float pxl = (float)(ix0 + lx) + 0.5f;
-                for (int y = iy0 + ly; y <= iy1; y += 4) {
+                auto row = [&](int y) {
                     const float dy = __fsub_rn((float)y + 0.5f, c4.w);
                     const int prow = (y - y0) * TW - x0 + ix0 + lx;
 #pragma unroll
@@ -345,9 +345,16 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
                         if (k1) fragment(dx1, dy, prow + 8 * (q + 1), f1);
                         if (!in1) break;
                     }
+                };
+                if constexpr (FULL) {
+                    // The whole tile: TH / 4 rows per lane.
+#pragma unroll
+                    for (int r = 0; r < TH / 4; ++r) row(y0 + ly + 4 * r);
+                } else {
+                    for (int y = iy0 + ly; y <= iy1; y += 4) row(y);
                 }
             };
-            const bool full = ix0 == x0 && ix1 == x0 + TW - 1;
+            const bool full = ix0 == x0 && ix1 == x0 + TW - 1 && iy0 == y0 && iy1 == y0 + TH - 1;
             if (may_core) {
                 if (may_clamp) walk(Flag<true>{}, Flag<true>{}, Flag<false>{});
                 else walk(Flag<true>{}, Flag<false>{}, Flag<false>{});
