@@ -138,7 +138,13 @@ typedef struct {
  *           entry may be NULL). htgs_render records [0]/[1] around the
  *           preprocess, [2]/[3] around binning and sorting and [4]/[5]
  *           around the blend; htgs_render_backward records [0]/[1] around
- *           the blend adjoint and [2]/[3] around the preprocess adjoint. */
+ *           the blend adjoint and [2]/[3] around the preprocess adjoint.
+ *           Without events a call launches each of its kernels as a
+ *           programmatic dependent of the one before (its CTAs may be
+ *           scheduled while the previous kernel finishes; it waits for that
+ *           kernel's completion before touching memory); with any event set
+ *           the kernels are launched plainly, so that the events mark the
+ *           phase boundaries. The results are the same either way. */
 typedef struct {
     int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16 (default), 32x16, 16x8 or 8x8 */
     int32_t px_per_thread;    /* pixels per thread in the forward blend: 1 (default), 2 or 4, a
