@@ -250,10 +250,12 @@ __global__ void __launch_bounds__(kBwdThreads, 3) blend_bwd_kernel(const __grid_
             float wmax = 0.f;  // largest blending weight of the record in this tile
             bool touched = false;
             const int lx = lane & 7, ly = lane >> 3;
-            // The walk over the record's box, compiled for each case of the
-            // two record-wide conditions: whether a fragment can belong to a
-            // core of this tile (most records of a deep tile cannot), and
-            // whether its alpha can reach the clamp.
+            // The walk over the record's box, compiled for each case of three
+            // record-wide conditions: whether a fragment can belong to a core
+            // of this tile (most records of a deep tile cannot), whether its
+            // alpha can reach the clamp, and (for the common case of neither)
+            // whether its box covers the whole tile, whose rows are then an
+            // unrolled loop without column bounds.
             auto walk = [&](auto core_flag, auto clamp_flag, auto full_flag) {
                 constexpr bool CORE = decltype(core_flag)::value;
                 constexpr bool CLAMP = decltype(clamp_flag)::value;
