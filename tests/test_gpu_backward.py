@@ -59,6 +59,24 @@ def test_small_scene_gradients(degree, K, tile, ppt, floor):
     assert_grad_close(got, ref, floor=floor, label=f"small scene degree={degree} K={K} {tile} ppt={ppt}")
 
 
+@pytest.mark.parametrize("K", [0, 8])
+def test_clamped_opacity_gradients(K):
+    """A third of the Gaussians have o = 0.9995 > alpha_max = 0.999, so alpha
+    is clamped near their centres (no gradient to the geometry there) and the
+    adjoint takes its walk with the clamp test for those records."""
+    scene = scenes.small_box_scene(64, seed=4, sh_degree=1)
+    cam = scenes.identity_camera(1200, 800, 1200.0).crop(584, 384, 32, 32).rounded()
+    prm = scenes.Params(K=K, bg=(0.1, 0.2, 0.3))
+    scene.means[:, :2] *= np.float32(0.04)
+    scene.opacity_logits[::3] = np.float32(np.log(0.9995 / 0.0005))
+    dl, d = _masked_upstream(scene, cam, prm, seed=17 + K)
+    ref = oracle.render_backward(scene.astype(np.float64), cam, prm, dl.astype(np.float64))
+    got, _ = _gpu_grads(scene, cam, prm, dl)
+    # Floor 2e-3: at K = 0 one log-scale element (1e-3 of the largest) is off
+    # by 1.9e-6 of the largest (ratio 1.84 at 1e-3); the norm error is 7.6e-6.
+    assert_grad_close(got, ref, floor=2e-3, label=f"clamped opacities K={K}")
+
+
 def test_no_tail_gradients():
     scene = scenes.small_box_scene(64, seed=7, sh_degree=1)
     cam = scenes.identity_camera(1200, 800, 1200.0).crop(584, 384, 32, 32).rounded()
