@@ -761,12 +761,25 @@ def main():
     # the render of step i: the render waits for its inputs and for the
     # read-back of the image buffer it overwrites, an upload waits for the
     # render that last read its buffer.
+    # The five parameter arrays sit in one pinned host buffer and, per slot,
+    # in one device buffer (each array starting on a 16-byte boundary), so a
+    # step's upload is a single copy; the renders take views of the device
+    # buffer.
     keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
-    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).pin_memory() for k in keys}
+    arrs = [np.ascontiguousarray(getattr(scene, k), dtype=np.float32) for k in keys]
+    offs, o = [], 0
+    for arr in arrs:
+        offs.append(o)
+        o += -(-arr.size // 4) * 4
+    host_all = torch.zeros(o, dtype=torch.float32).pin_memory()
+    for arr, off in zip(arrs, offs):
+        host_all[off:off + arr.size] = torch.from_numpy(arr.ravel())
     host_img = [torch.empty(image.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
-    h2d = sum(t.numel() * 4 for t in host.values())
+    h2d = host_all.numel() * 4
     d2h = host_img[0].numel() * 4
-    dev = [g, GaussianTensors(*[torch.empty_like(getattr(g, k)) for k in keys], g.sh_degree)]
+    dev_all = [torch.empty(o, dtype=torch.float32, device="cuda") for _ in range(2)]
+    dev = [GaussianTensors(*[buf[off:off + arr.size].view(arr.shape) for arr, off in zip(arrs, offs)],
+                           g.sh_degree) for buf in dev_all]
     imgs = [image, torch.empty_like(image)]
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     inputs_ready = [torch.cuda.Event() for _ in range(2)]
@@ -778,8 +791,7 @@ def main():
         b = i % 2
         up.wait_event(inputs_free[b])
         with torch.cuda.stream(up):
-            for k in keys:
-                getattr(dev[b], k).copy_(host[k], non_blocking=True)
+            dev_all[b].copy_(host_all, non_blocking=True)
         inputs_ready[b].record(up)
         stream.wait_event(inputs_ready[b])
         stream.wait_event(image_free[b])
@@ -815,12 +827,11 @@ def main():
     l0.record(up)
     with torch.cuda.stream(up):
         for _ in range(5):
-            for k in keys:
-                getattr(dev[1], k).copy_(host[k], non_blocking=True)
+            dev_all[1].copy_(host_all, non_blocking=True)
     l1.record(up)
     torch.cuda.synchronize()
     link_gbs = 5 * h2d / (l0.elapsed_time(l1) * 1e-3) / 1e9
-    del dev[1], imgs[1]
+    del dev, dev_all, imgs[1]
 
     # ---- training step: render + L1 + backward (500k Gaussians, 1200x800) --
     tscene, ttarget, tcam, tprm = scenes.config3(seed=2 + rank)
