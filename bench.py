@@ -820,17 +820,21 @@ def main():
     e2e_fps = job_throughput(args.steps, world, e2e_ms)
     last = (args.steps - 1) % 2
     assert torch.equal(host_img[last], imgs[last].cpu()), "the read-back image must be the render's"
-    # The host link's own rate: one step's uploads alone, back to back. It
-    # bounds the end-to-end rate at h2d bytes / rate, whatever the render does.
-    torch.cuda.synchronize()
-    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0.record(up)
-    with torch.cuda.stream(up):
-        for _ in range(5):
-            dev_all[1].copy_(host_all, non_blocking=True)
-    l1.record(up)
-    torch.cuda.synchronize()
-    link_gbs = 5 * h2d / (l0.elapsed_time(l1) * 1e-3) / 1e9
+    # The host link's own rate: one step's uploads alone, back to back (the
+    # best of three rounds of five, as the host's memory is shared with other
+    # work). It bounds the end-to-end rate at h2d bytes / rate, whatever the
+    # render does.
+    link_gbs = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(up)
+        with torch.cuda.stream(up):
+            for _ in range(5):
+                dev_all[1].copy_(host_all, non_blocking=True)
+        l1.record(up)
+        torch.cuda.synchronize()
+        link_gbs = max(link_gbs, 5 * h2d / (l0.elapsed_time(l1) * 1e-3) / 1e9)
     del dev, dev_all, imgs[1]
 
     # ---- training step: render + L1 + backward (500k Gaussians, 1200x800) --
