@@ -32,9 +32,9 @@ namespace htgs {
 constexpr int kStageF4 = kRecF4 + 1;
 
 // Dynamic shared memory of the forward: three staging buffers of B records
-// (B = htgs_launch.smem_batch: 32, 64 or 128).
+// (B = htgs_launch.smem_batch: 32, 64 or 128) and three of B record ids.
 __host__ __device__ inline size_t fwd_smem_bytes(int B) {
-    return (size_t)3 * B * kStageF4 * sizeof(float4);
+    return (size_t)3 * B * kStageF4 * sizeof(float4) + (size_t)3 * B * sizeof(uint32_t);
 }
 
 // Alpha of one record at a pixel from its (Q, D) pair, evaluated identically
@@ -110,6 +110,7 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     // bank conflicts of the per-lane cull loads but costs registers, and
     // measured 10-15% slower.)
     float4 *const s_rec = s_dyn;  // [3][B][kStageF4]
+    uint32_t *const s_ids = reinterpret_cast<uint32_t *>(s_rec + 3 * B * kStageF4);  // [3][B]
     __shared__ int s_item;
     __shared__ int s_last;
     if (a.status[kStError] != 0) return;
@@ -173,28 +174,52 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     // Stage batch b into buffer b % 3: each thread fetches the ids of the
     // records it copies (8 threads per record read the same id), so no
     // barrier separates the id loads from the copies.
-    auto issue = [&](int b) {
+    // Staging of batch b's records into buffer b % 3; their ids come from
+    // the id buffer b % 3 (staged by cp.async two iterations earlier) or,
+    // for the first two batches, from global memory.
+    auto issue = [&](int b, bool ids_staged) {
+        if (b >= nbatches) return;
         const int nb = batch_size(b);
         const uint32_t base = range.x + (uint32_t)b * B;
         float4 *dst = s_rec + (size_t)(b % 3) * B * kStageF4;
+        const uint32_t *ids = s_ids + (b % 3) * B;
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
-            const uint32_t gid = a.vals[base + j];
+            const uint32_t gid = ids_staged ? ids[j] : a.vals[base + j];
             if (f == 0) reinterpret_cast<uint32_t *>(dst + j * kStageF4 + kRecF4)[0] = gid;
             cp_async16(dst + j * kStageF4 + f, a.rec + (size_t)gid * kRecF4 + f);
         }
-        cp_async_commit();
     };
-    // Two batches in flight, one barrier per batch: after it, batch b is
-    // visible to every thread and every thread has finished batch b - 1,
-    // whose buffer the copies of batch b + 2 then overwrite.
-    if (nbatches > 0) issue(0);
-    if (nbatches > 1) issue(1);
+    // Staging of batch b's record ids into id buffer b % 3.
+    auto issue_ids = [&](int b) {
+        if (b >= nbatches) return;
+        const int nb = batch_size(b);
+        const uint32_t base = range.x + (uint32_t)b * B;
+        for (int j = tid; j < nb; j += NT) cp_async4(s_ids + (b % 3) * B + j, a.vals + base + j);
+    };
+    // Two batches of records in flight, their ids two batches further
+    // ahead, so that no record copy waits on a global load of its id. Every
+    // iteration commits two groups (records of b + 2, ids of b + 4; either
+    // may be empty), so waiting until two groups remain pending completes
+    // the records of b and the ids of b + 2. One barrier per batch: after it,
+    // those are visible to every thread and every thread has finished batch
+    // b - 1, whose record buffer the copies of batch b + 2 then overwrite
+    // (and the ids of b + 1, whose buffer the ids of b + 4 take).
+    issue(0, false);
+    cp_async_commit();
+    issue_ids(2);
+    cp_async_commit();
+    issue(1, false);
+    cp_async_commit();
+    issue_ids(3);
+    cp_async_commit();
     for (int b = 0; b < nbatches; ++b) {
-        if (b + 1 < nbatches) cp_async_wait<1>();
-        else cp_async_wait<0>();
+        cp_async_wait<2>();
         __syncthreads();
-        if (b + 2 < nbatches) issue(b + 2);
+        issue(b + 2, true);
+        cp_async_commit();
+        issue_ids(b + 4);
+        cp_async_commit();
         const int nb = batch_size(b);
         const float4(*rec)[kStageF4] =
             reinterpret_cast<const float4(*)[kStageF4]>(s_rec + (size_t)(b % 3) * B * kStageF4);
