@@ -171,9 +171,6 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     const uint2 range = chunk_range(a.ranges[tile], chunk_k, chunk_m);
     const int nbatches = (int)((range.y - range.x + B - 1) / B);
     auto batch_size = [&](int b) { return (int)min((uint32_t)B, range.y - range.x - (uint32_t)b * B); };
-    // Stage batch b into buffer b % 3: each thread fetches the ids of the
-    // records it copies (8 threads per record read the same id), so no
-    // barrier separates the id loads from the copies.
     // Staging of batch b's records into buffer b % 3; their ids come from
     // the id buffer b % 3 (staged by cp.async two iterations earlier) or,
     // for the first two batches, from global memory.
