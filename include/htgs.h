@@ -153,7 +153,9 @@ typedef struct {
                                  as 2, 16x8 and 8x8 return HTGS_ERR_NOT_SUPPORTED) */
     int32_t depth_bits;       /* reserved; must be 0 (the sort key is the tile id alone) */
     int32_t smem_batch;       /* records the forward blend stages per shared-memory batch:
-                                 32, 64 or 128 (default, also for 0) */
+                                 32, 64, 128 (default, also for 0) or 192 (two staging
+                                 buffers instead of three, in the same shared memory; the
+                                 variant without per-pixel hybrid transparency takes 128) */
     void *events[6];
     int32_t test_lookback_stall; /* test of the failure path, 0 otherwise: in the tile sort's first
                                     digit pass the first block also waits for a look-back word that

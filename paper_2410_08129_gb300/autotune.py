@@ -18,8 +18,9 @@ from . import binding as B
 # (tile shape, forward pixels per thread) candidates compiled into the library.
 CANDIDATES = [((16, 16), 1), ((16, 16), 2), ((32, 16), 1), ((32, 16), 2), ((16, 8), 1), ((16, 8), 2), ((8, 8), 1),
               ((8, 8), 2)]
-# Records per shared-memory batch of the forward blend (the first is the default).
-BATCHES = (128, 64, 32)
+# Records per shared-memory batch of the forward blend (the first is the default;
+# 192 stages into two buffers instead of three).
+BATCHES = (128, 192, 64, 32)
 
 _cache: dict = {}
 

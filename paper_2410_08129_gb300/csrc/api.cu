@@ -49,7 +49,7 @@ bool tile_shape(const htgs_launch *launch, TileArgs &t) {
     t.cover = launch ? launch->tile_cover : 0;
     const bool shape_ok = (t.tile_w == 16 && t.tile_h == 16) || (t.tile_w == 16 && t.tile_h == 8) ||
                           (t.tile_w == 8 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 16);
-    const bool batch_ok = t.batch == 32 || t.batch == 64 || t.batch == 128;
+    const bool batch_ok = t.batch == 32 || t.batch == 64 || t.batch == 128 || t.batch == 192;
     return shape_ok && batch_ok && t.depth_bits == 0;
 }
 

@@ -31,10 +31,16 @@ namespace htgs {
 // serialises eight ways.
 constexpr int kStageF4 = kRecF4 + 1;
 
-// Dynamic shared memory of the forward: three staging buffers of B records
-// (B = htgs_launch.smem_batch: 32, 64 or 128) and three of B record ids.
+// Staging buffers of the forward for B records per batch
+// (B = htgs_launch.smem_batch: 32, 64, 128 or 192): three, so that two
+// batches are in flight while one is evaluated, or two for 192-record
+// batches (the same shared memory as three of 128; one batch in flight).
+__host__ __device__ inline int fwd_buffers(int B) { return B > 128 ? 2 : 3; }
+
+// Dynamic shared memory of the forward: the staging buffers of B records
+// and as many buffers of B record ids.
 __host__ __device__ inline size_t fwd_smem_bytes(int B) {
-    return (size_t)3 * B * kStageF4 * sizeof(float4) + (size_t)3 * B * sizeof(uint32_t);
+    return (size_t)fwd_buffers(B) * B * (kStageF4 * sizeof(float4) + sizeof(uint32_t));
 }
 
 // Alpha of one record at a pixel from its (Q, D) pair, evaluated identically
@@ -109,8 +115,9 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     // (Moving the cull words 6 and 7 to arrays of their own also removes the
     // bank conflicts of the per-lane cull loads but costs registers, and
     // measured 10-15% slower.)
-    float4 *const s_rec = s_dyn;  // [3][B][kStageF4]
-    uint32_t *const s_ids = reinterpret_cast<uint32_t *>(s_rec + 3 * B * kStageF4);  // [3][B]
+    const int NBUF = fwd_buffers(B);
+    float4 *const s_rec = s_dyn;  // [NBUF][B][kStageF4]
+    uint32_t *const s_ids = reinterpret_cast<uint32_t *>(s_rec + NBUF * B * kStageF4);  // [NBUF][B]
     __shared__ int s_item;
     __shared__ int s_last;
     if (a.status[kStError] != 0) return;
@@ -171,15 +178,15 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     const uint2 range = chunk_range(a.ranges[tile], chunk_k, chunk_m);
     const int nbatches = (int)((range.y - range.x + B - 1) / B);
     auto batch_size = [&](int b) { return (int)min((uint32_t)B, range.y - range.x - (uint32_t)b * B); };
-    // Staging of batch b's records into buffer b % 3; their ids come from
-    // the id buffer b % 3 (staged by cp.async two iterations earlier) or,
-    // for the first two batches, from global memory.
+    // Staging of batch b's records into buffer b % NBUF; their ids come
+    // from the id buffer b % NBUF (staged by cp.async earlier) or, for the
+    // first batches, from global memory.
     auto issue = [&](int b, bool ids_staged) {
         if (b >= nbatches) return;
         const int nb = batch_size(b);
         const uint32_t base = range.x + (uint32_t)b * B;
-        float4 *dst = s_rec + (size_t)(b % 3) * B * kStageF4;
-        const uint32_t *ids = s_ids + (b % 3) * B;
+        float4 *dst = s_rec + (size_t)(b % NBUF) * B * kStageF4;
+        const uint32_t *ids = s_ids + (b % NBUF) * B;
         for (int k = tid; k < nb * kRecF4; k += NT) {
             const int j = k / kRecF4, f = k - j * kRecF4;
             const uint32_t gid = ids_staged ? ids[j] : a.vals[base + j];
@@ -187,12 +194,12 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
             cp_async16(dst + j * kStageF4 + f, a.rec + (size_t)gid * kRecF4 + f);
         }
     };
-    // Staging of batch b's record ids into id buffer b % 3.
+    // Staging of batch b's record ids into id buffer b % NBUF.
     auto issue_ids = [&](int b) {
         if (b >= nbatches) return;
         const int nb = batch_size(b);
         const uint32_t base = range.x + (uint32_t)b * B;
-        for (int j = tid; j < nb; j += NT) cp_async4(s_ids + (b % 3) * B + j, a.vals + base + j);
+        for (int j = tid; j < nb; j += NT) cp_async4(s_ids + (b % NBUF) * B + j, a.vals + base + j);
     };
     // Two batches of records in flight, their ids two batches further
     // ahead, so that no record copy waits on a global load of its id. Every
@@ -202,24 +209,41 @@ blend_fwd_kernel(const __grid_constant__ Batch bt, BlendFwdArgs a) {
     // those are visible to every thread and every thread has finished batch
     // b - 1, whose record buffer the copies of batch b + 2 then overwrite
     // (and the ids of b + 1, whose buffer the ids of b + 4 take).
-    issue(0, false);
-    cp_async_commit();
-    issue_ids(2);
-    cp_async_commit();
-    issue(1, false);
-    cp_async_commit();
-    issue_ids(3);
-    cp_async_commit();
+    // With two buffers (192-record batches) one batch of records is in
+    // flight and its ids one batch further ahead: every iteration waits for
+    // all copies, then issues the records of b + 1 and the ids of b + 2.
+    if (NBUF == 3) {
+        issue(0, false);
+        cp_async_commit();
+        issue_ids(2);
+        cp_async_commit();
+        issue(1, false);
+        cp_async_commit();
+        issue_ids(3);
+        cp_async_commit();
+    } else {
+        issue(0, false);
+        issue_ids(1);
+        cp_async_commit();
+    }
     for (int b = 0; b < nbatches; ++b) {
-        cp_async_wait<2>();
-        __syncthreads();
-        issue(b + 2, true);
-        cp_async_commit();
-        issue_ids(b + 4);
-        cp_async_commit();
+        if (NBUF == 3) {
+            cp_async_wait<2>();
+            __syncthreads();
+            issue(b + 2, true);
+            cp_async_commit();
+            issue_ids(b + 4);
+            cp_async_commit();
+        } else {
+            cp_async_wait<0>();
+            __syncthreads();
+            issue(b + 1, true);
+            issue_ids(b + 2);
+            cp_async_commit();
+        }
         const int nb = batch_size(b);
         const float4(*rec)[kStageF4] =
-            reinterpret_cast<const float4(*)[kStageF4]>(s_rec + (size_t)(b % 3) * B * kStageF4);
+            reinterpret_cast<const float4(*)[kStageF4]>(s_rec + (size_t)(b % NBUF) * B * kStageF4);
         for (int c = 0; c < nb; c += 32) {
             // Lane c + l tests record c + l against the warp's footprint:
             // its box, then the axis n = A v through the cutoff ellipse
@@ -462,7 +486,9 @@ bool run_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / PPT;
     const void *fn = (const void *)blend_fwd_kernel<KMAX, TW, TH, PPT, NOTAIL>;
     const size_t smem = fwd_smem_bytes(a.tiles.batch);
-    if (!allow_dynamic_smem(fn, fwd_smem_bytes(128))) return false;
+    if (!allow_dynamic_smem(fn, fwd_smem_bytes(128) > fwd_smem_bytes(192) ? fwd_smem_bytes(128)
+                                                                          : fwd_smem_bytes(192)))
+        return false;
     const int grid = persistent_grid(fn, NT, smem, a.max_items);
     launch_k(blend_fwd_kernel<KMAX, TW, TH, PPT, NOTAIL>, grid, NT, smem, s, b, a);
     return true;

@@ -335,10 +335,13 @@ blend_sorted_bwd_kernel(const __grid_constant__ Batch bt, BlendBwdArgs a) {
 template <int TW, int TH>
 bool run_sorted_fwd(const Batch &b, const BlendFwdArgs &a, cudaStream_t s) {
     const void *fn = (const void *)blend_sorted_fwd_kernel<TW, TH>;
-    const size_t smem = sorted_fwd_smem_bytes(a.tiles.batch);
+    // (At most 128 records per batch: three buffers of 192 would not fit.)
+    BlendFwdArgs args = a;
+    if (args.tiles.batch > 128) args.tiles.batch = 128;
+    const size_t smem = sorted_fwd_smem_bytes(args.tiles.batch);
     if (!allow_dynamic_smem(fn, sorted_fwd_smem_bytes(128))) return false;
-    const int grid = persistent_grid(fn, TW * TH, smem, a.max_items);
-    launch_k(blend_sorted_fwd_kernel<TW, TH>, grid, TW * TH, smem, s, b, a);
+    const int grid = persistent_grid(fn, TW * TH, smem, args.max_items);
+    launch_k(blend_sorted_fwd_kernel<TW, TH>, grid, TW * TH, smem, s, b, args);
     return true;
 }
 

@@ -23,14 +23,14 @@ def test_coordinate_search_picks_the_fastest():
     def ms(k):
         (tw, th), ppt, b = k
         base = {(32, 16): 1.0, (16, 16): 1.2}.get((tw, th), 2.0) + 0.3 * (ppt - 1)
-        return base + {128: 0.05, 64: 0.0, 32: 0.1}[b]
+        return base + {128: 0.05, 192: 0.02, 64: 0.0, 32: 0.1}[b]
     calls = []
     launch, times = at.autotune(lambda L: None, candidates=at.CANDIDATES, timer=_fake(ms, calls))
     assert ((launch.tile_w, launch.tile_h), launch.px_per_thread, launch.smem_batch) == ((32, 16), 1, 64)
-    # every candidate at batch 128, then 64 and 32 for the winner only
+    # every candidate at batch 128, then 192, 64 and 32 for the winner only
     assert calls[:len(at.CANDIDATES)] == [(t, p, 128) for t, p in at.CANDIDATES]
-    assert calls[len(at.CANDIDATES):] == [((32, 16), 1, 64), ((32, 16), 1, 32)]
-    assert len(times) == len(at.CANDIDATES) + 2
+    assert calls[len(at.CANDIDATES):] == [((32, 16), 1, 192), ((32, 16), 1, 64), ((32, 16), 1, 32)]
+    assert len(times) == len(at.CANDIDATES) + 3
 
 
 def test_unsupported_candidates_are_skipped_and_results_cached():

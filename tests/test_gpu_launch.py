@@ -39,3 +39,23 @@ def test_dependent_and_plain_launches_agree(K):
     for k in ga:
         scale = max(float(np.abs(ga[k]).max()), 1e-30)
         assert np.abs(ga[k] - gb[k]).max() <= 1e-5 * scale, k
+
+
+def test_staging_batch_sizes_agree():
+    """The forward's staging batch (32, 64 or 128 records in three buffers,
+    192 in two) changes only the schedule: the image and saved state are the
+    same bit for bit."""
+    scene = scenes.small_box_scene(20000, seed=12, sh_degree=1)
+    cam = scenes.identity_camera(320, 208, 300.0).rounded()
+    prm = scenes.Params(K=8, bg=(0.1, 0.2, 0.3))
+    g = GaussianTensors.from_scene(scene)
+    outs = []
+    for batch in (128, 192, 64, 32):
+        r = Renderer(cam, prm, scene.n, launch=B.c_launch((16, 16), 1, smem_batch=batch))
+        img = r.forward(g, save=True)
+        torch.cuda.synchronize()
+        assert r.status()[0] == B.HTGS_OK
+        outs.append((img.cpu().numpy(), r.saved.cpu().numpy().view(np.uint32)))
+    for img, saved in outs[1:]:
+        assert np.array_equal(img, outs[0][0])
+        assert np.array_equal(saved, outs[0][1])
