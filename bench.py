@@ -478,12 +478,12 @@ def batched_leg(steps, warmup):
     return out
 
 
-def profile_case(which: str, warmup: int, tile=None, ppt: int = 1, binning: int = 0):
+def profile_case(which: str, warmup: int, tile=None, ppt: int = 1, binning: int = 0, batch: int = 128):
     """A few untimed steps of the headline render (fwd) or of the training
     step (train): `warmup` steps, then 2 more, nothing else on the GPU. The
     launch shape defaults to the one the autotuner picks for the workload on
     a GB300 (16x16 for the render, 32x16 for the training step, 1 pixel per
-    thread)."""
+    thread); `batch` is the forward's staging batch."""
     import torch
     from paper_2410_08129_gb300 import binding as B
     from paper_2410_08129_gb300 import scenes
@@ -491,7 +491,7 @@ def profile_case(which: str, warmup: int, tile=None, ppt: int = 1, binning: int 
     if which == "fwd":
         scene, cam, prm = scenes.config2()
         g = GaussianTensors.from_scene(scene)
-        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (16, 16), ppt, binning=binning))
+        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (16, 16), ppt, binning=binning, smem_batch=batch))
         img = r.image_buffer()
         r.forward(g, image=img, save=False, check=True)
         for _ in range(warmup + 2):
@@ -499,7 +499,7 @@ def profile_case(which: str, warmup: int, tile=None, ppt: int = 1, binning: int 
     else:
         scene, target, cam, prm = scenes.config3()
         g = GaussianTensors.from_scene(scene)
-        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (32, 16), ppt, binning=binning))
+        r = Renderer(cam.rounded(), prm, scene.n, launch=B.c_launch(tile or (32, 16), ppt, binning=binning, smem_batch=batch))
         img = r.image_buffer()
         tgt = r.forward(GaussianTensors.from_scene(target), save=False, check=True).clone()
         dl = torch.empty_like(img)
@@ -531,6 +531,8 @@ def main():
     ap.add_argument("--profile-ppt", type=int, default=1, help="forward pixels per thread of --profile")
     ap.add_argument("--profile-binning", choices=["radix", "counting"], default="radix",
                     help="tile binning of --profile (the lists are the same)")
+    ap.add_argument("--profile-batch", type=int, default=128, choices=[32, 64, 128, 192],
+                    help="forward staging batch of --profile")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -538,7 +540,7 @@ def main():
     if args.profile:
         tile = tuple(int(v) for v in args.profile_tile.split("x")) if args.profile_tile else None
         profile_case(args.profile, args.warmup, tile, args.profile_ppt,
-                     binning=2 if args.profile_binning == "counting" else 1)
+                     binning=2 if args.profile_binning == "counting" else 1, batch=args.profile_batch)
         return
 
     import torch
