@@ -386,6 +386,8 @@ __global__ void ranges_kernel(RangeArgs a) {
 // Blend work items (one CTA): chunk the long tile lists, then bucket the
 // items by chunk length (two buckets per octave, longest first).
 // ---------------------------------------------------------------------------
+constexpr int kSchedUnroll = 4;  // tiles per thread and step of the schedule kernel
+
 __device__ __forceinline__ int length_bucket(uint32_t len) {
     if (len == 0) return kSchedBuckets - 1;
     const int l = 31 - __clz(len);
@@ -463,29 +465,56 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(ScheduleArgs a)
     for (int b = tid; b < kSchedBuckets; b += kSchedThreads) s_cnt[b] = 0;
     if (tid == 0) s_slots = 0;
     __syncthreads();
-    for (int t = tid; t < a.n_tiles; t += kSchedThreads) {
-        const uint2 r = a.ranges[t];
-        const uint32_t cnt = r.y - r.x;
-        const int m = parts(cnt);
-        atomicAdd(&s_cnt[length_bucket((cnt + m - 1) / (uint32_t)m)], (uint32_t)m);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < kSchedBuckets; ++b) {
-            s_pos[b] = run;
-            run += s_cnt[b];
+    // Each thread takes kSchedUnroll tiles per step and loads their ranges
+    // before any of its shared-memory atomics, so that the loads overlap.
+    const int T = a.n_tiles;
+    auto load_counts = [&](int t0, uint32_t (&cnt)[kSchedUnroll]) {
+#pragma unroll
+        for (int u = 0; u < kSchedUnroll; ++u) {
+            const int t = t0 + u * kSchedThreads;
+            const uint2 r = t < T ? a.ranges[t] : make_uint2(0u, 0u);
+            cnt[u] = r.y - r.x;
         }
-        *a.n_items = run;
+    };
+    for (int t0 = tid; t0 < T; t0 += kSchedThreads * kSchedUnroll) {
+        uint32_t cnt[kSchedUnroll];
+        load_counts(t0, cnt);
+#pragma unroll
+        for (int u = 0; u < kSchedUnroll; ++u) {
+            if (t0 + u * kSchedThreads >= T) break;
+            const int m = parts(cnt[u]);
+            atomicAdd(&s_cnt[length_bucket((cnt[u] + m - 1) / (uint32_t)m)], (uint32_t)m);
+        }
     }
     __syncthreads();
-    for (int t = tid; t < a.n_tiles; t += kSchedThreads) {
-        const uint2 r = a.ranges[t];
-        const uint32_t cnt = r.y - r.x;
-        const int m = parts(cnt);
-        const int slot0 = m > 1 ? (int)atomicAdd(&s_slots, (uint32_t)m) : 0;
-        const uint32_t pos = atomicAdd(&s_pos[length_bucket((cnt + m - 1) / (uint32_t)m)], (uint32_t)m);
-        for (int k = 0; k < m; ++k) a.items[pos + k] = make_int4(t, k, m, slot0);
+    // Bucket offsets: an exclusive scan of the 64 bucket counts by one warp,
+    // two buckets per lane.
+    static_assert(kSchedBuckets == 64, "two buckets per lane of one warp");
+    if (tid < 32) {
+        const uint32_t c0 = s_cnt[2 * tid], c1 = s_cnt[2 * tid + 1];
+        uint32_t incl = c0 + c1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (tid >= o) incl += x;
+        }
+        const uint32_t excl = incl - (c0 + c1);
+        s_pos[2 * tid] = excl;
+        s_pos[2 * tid + 1] = excl + c0;
+        if (tid == 31) *a.n_items = incl;
+    }
+    __syncthreads();
+    for (int t0 = tid; t0 < T; t0 += kSchedThreads * kSchedUnroll) {
+        uint32_t cnt[kSchedUnroll];
+        load_counts(t0, cnt);
+#pragma unroll
+        for (int u = 0; u < kSchedUnroll; ++u) {
+            const int t = t0 + u * kSchedThreads;
+            if (t >= T) break;
+            const int m = parts(cnt[u]);
+            const int slot0 = m > 1 ? (int)atomicAdd(&s_slots, (uint32_t)m) : 0;
+            const uint32_t pos = atomicAdd(&s_pos[length_bucket((cnt[u] + m - 1) / (uint32_t)m)], (uint32_t)m);
+            for (int k = 0; k < m; ++k) a.items[pos + k] = make_int4(t, k, m, slot0);
+        }
     }
 }
 
