@@ -132,6 +132,32 @@ def recorded_traffic():
     return rec.get("bytes_per_launch_1080p_1M") if digest == rec.get("sources_code_sha256") else None
 
 
+def dist_summary(ms) -> dict:
+    """Median, mean and extremes of per-step times (ms)."""
+    a = np.asarray(ms, dtype=np.float64)
+    return {"n": int(a.size), "median": float(np.median(a)), "mean": float(a.mean()),
+            "min": float(a.min()), "max": float(a.max())}
+
+
+def per_step_ms(step, stream, warmup: int, n: int) -> dict:
+    """`warmup` untimed calls of `step`, then `n` timed ones with a CUDA event
+    recorded on `stream` between consecutive calls (the events sit between
+    steps, never inside one)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    ev[0].record(stream)
+    for i in range(n):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    out = dist_summary([ev[i].elapsed_time(ev[i + 1]) for i in range(n)])
+    out["note"] = f"{warmup} warm-ups, {n} steps, an event between consecutive steps"
+    return out
+
+
 def reduce_max(x: float, world: int, device) -> float:
     """Largest value of x over the ranks of the default process group (the
     job's time is that of its slowest rank)."""
@@ -616,6 +642,9 @@ def main():
         bin_ms.append(ev[2].elapsed_time(ev[3]))
         blend_ms.append(ev[4].elapsed_time(ev[5]))
     r.launch = launch
+    # Per-frame distribution (10 warm-ups, then 100 frames, an event between
+    # consecutive frames): median and mean of the frame time.
+    frame_dist = per_step_ms(lambda: r.forward(g, image=image, save=False, check=False), stream, 10, 100)
     st, inst = r.status()
     assert st == B.HTGS_OK, B.htgs_status_string(st)
     counters = B.htgs_get_counters(r.workspace)
@@ -884,16 +913,23 @@ def main():
     torch.cuda.synchronize()
     n_train = max(5, args.steps // 5)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # An event between consecutive steps as well, for the per-step
+    # distribution (one record per 80 ms step).
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_train - 1)]
     with ClockSampler(local) as train_clocks:
         barrier()
         torch.cuda.synchronize()
         s0.record(stream)
-        for _ in range(n_train):
+        for i in range(n_train):
             train_step()
+            if i + 1 < n_train:
+                step_ev[i].record(stream)
         s1.record(stream)
         torch.cuda.synchronize()
         barrier()
     train_ms = max_over_ranks(s0.elapsed_time(s1)) / n_train
+    marks = [s0] + step_ev + [s1]
+    train_dist = dist_summary([marks[i].elapsed_time(marks[i + 1]) for i in range(n_train)])
     bwd_blend_ms, fwd_blend_train_ms = [], []
     tr.launch = tlaunch_ev
     for _ in range(3):
@@ -1080,10 +1116,12 @@ def main():
                    "smem_batch": fwd_shape[2], "parallelism": f"replicas{world}",
                    "autotune_ms": {f"{t[0]}x{t[1]}/ppt{pp}/b{bb}": round(v, 4) for (t, pp, bb), v in tune_fwd.items()},
                    "l2": "inputs larger than L2 (236 MB of Gaussian parameters per frame)"},
+        "frame_ms": frame_dist,
         "phases_ms": {"preprocess": float(np.mean(pre_ms)), "binning_sort": float(np.mean(bin_ms)),
                       "blend": float(np.mean(blend_ms))},
         "instances": inst, "counters": counters,
         "fwd_bwd": {"value": job_throughput(1, world, train_ms), "unit": "steps/s", "ms_per_step": train_ms,
+                    "step_ms": train_dist,
                     "workload": "500k Gaussians (box distribution), 1200x800, K=8: render + L1 + backward",
                     "launch": {"tile": f"{train_shape[0][0]}x{train_shape[0][1]}", "px_per_thread": train_shape[1],
                                "smem_batch": train_shape[2],

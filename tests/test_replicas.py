@@ -65,3 +65,8 @@ def test_views_are_split_under_the_instance_limit():
     assert bench._chunks([5, 5, 5], 100) == [[0, 1, 2]]
     assert bench._chunks([60, 50, 30, 80], 100) == [[0], [1, 2], [3]]
     assert bench._chunks([150, 10], 100) == [[0], [1]]
+
+
+def test_step_time_summary():
+    d = bench.dist_summary([3.0, 1.0, 2.0, 10.0])
+    assert d == {"n": 4, "median": 2.5, "mean": 4.0, "min": 1.0, "max": 10.0}
