@@ -5,8 +5,9 @@
 // Forward: one CTA per tile of TW x TH pixels; each warp owns an 8 x (4 PPT)
 // pixel footprint and each lane PPT vertically adjacent pixels. The tile's
 // instance list (gid ascending, no depth order) is staged through shared
-// memory in batches of records, three buffers deep with cp.async so that the
-// gathers of the next two batches overlap the evaluation of the current one.
+// memory in batches of records with cp.async: three buffers deep, so that the
+// gathers of the next two batches overlap the evaluation of the current one,
+// or, for 192-record batches, two buffers deep (one batch in flight).
 // A warp first culls a batch against its footprint (per lane and record a
 // bounding-box test and one separating axis against the record's cutoff
 // ellipse; one ballot per 32 records) and evaluates only the records that
