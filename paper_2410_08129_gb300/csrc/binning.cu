@@ -371,14 +371,38 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a, int 
 // ---------------------------------------------------------------------------
 // Tile ranges from the sorted keys.
 // ---------------------------------------------------------------------------
+// Each thread takes kRangeKeys consecutive keys (two 16-byte loads) and
+// their two neighbours, all loaded before any is compared; a neighbour past
+// either end reads as a key no tile has.
+constexpr int kRangeKeys = 8;
+static_assert(kRangeKeys == 8, "two uint4 loads per thread");
+
 __global__ void ranges_kernel(RangeArgs a) {
     dependent_entry();
     const uint32_t total = *a.total;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const uint32_t t = a.keys[i];
-        if (t >= (uint32_t)a.n_tiles) continue;
-        if (i == 0 || a.keys[i - 1] != t) a.ranges[t].x = i;
-        if (i + 1 == total || a.keys[i + 1] != t) a.ranges[t].y = i + 1;
+    const uint32_t none = 0xffffffffu;
+    const uint32_t step = gridDim.x * blockDim.x * kRangeKeys;
+    for (uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * kRangeKeys; i0 < total; i0 += step) {
+        uint32_t k[kRangeKeys + 2];  // keys i0 - 1 .. i0 + kRangeKeys
+        k[0] = i0 > 0 ? a.keys[i0 - 1] : none;
+        if (i0 + kRangeKeys <= total) {
+            // i0 is a multiple of 8 and the key array 16-byte aligned.
+            const uint4 lo = *reinterpret_cast<const uint4 *>(a.keys + i0);
+            const uint4 hi = *reinterpret_cast<const uint4 *>(a.keys + i0 + 4);
+            k[1] = lo.x; k[2] = lo.y; k[3] = lo.z; k[4] = lo.w;
+            k[5] = hi.x; k[6] = hi.y; k[7] = hi.z; k[8] = hi.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kRangeKeys; ++j) k[1 + j] = i0 + j < total ? a.keys[i0 + j] : none;
+        }
+        k[kRangeKeys + 1] = i0 + kRangeKeys < total ? a.keys[i0 + kRangeKeys] : none;
+#pragma unroll
+        for (int j = 0; j < kRangeKeys; ++j) {
+            const uint32_t t = k[1 + j];
+            if (t >= (uint32_t)a.n_tiles) continue;  // also past the end
+            if (k[j] != t) a.ranges[t].x = i0 + j;
+            if (k[j + 2] != t) a.ranges[t].y = i0 + j + 1;
+        }
     }
 }
 
@@ -585,7 +609,7 @@ void launch_ranges(RangeArgs a, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    launch_k(ranges_kernel, sms * 8, 256, 0, s, a);
+    launch_k(ranges_kernel, sms * 8, 256, 0, s, a);  // 2.5M keys per sweep
 }
 
 namespace {
