@@ -165,11 +165,26 @@ __global__ void __launch_bounds__(kSortThreads) histogram_kernel(SortArgs a) {
     __syncthreads();
     const uint32_t total = *a.total;
     const uint32_t *keys = a.keys[0];
-    for (uint32_t idx = blockIdx.x * kSortThreads + threadIdx.x; idx < total;
-         idx += gridDim.x * kSortThreads) {
-        const uint32_t k = keys[idx];
-        for (int p = 0; p < a.passes; ++p)
-            atomicAdd(&h[p * kMaxRadix + ((k >> (p * a.digit_bits)) & (uint32_t)(R - 1))], 1u);
+    // Eight consecutive keys per thread (two 16-byte loads; the key array is
+    // 16-byte aligned), loaded before any of their counts is added.
+    const uint32_t step = gridDim.x * kSortThreads * 8;
+    for (uint32_t i0 = (blockIdx.x * kSortThreads + threadIdx.x) * 8; i0 < total; i0 += step) {
+        uint32_t k[8];
+        if (i0 + 8 <= total) {
+            const uint4 lo = *reinterpret_cast<const uint4 *>(keys + i0);
+            const uint4 hi = *reinterpret_cast<const uint4 *>(keys + i0 + 4);
+            k[0] = lo.x; k[1] = lo.y; k[2] = lo.z; k[3] = lo.w;
+            k[4] = hi.x; k[5] = hi.y; k[6] = hi.z; k[7] = hi.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) k[j] = i0 + j < total ? keys[i0 + j] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (i0 + j >= total) break;
+            for (int p = 0; p < a.passes; ++p)
+                atomicAdd(&h[p * kMaxRadix + ((k[j] >> (p * a.digit_bits)) & (uint32_t)(R - 1))], 1u);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < a.passes * kMaxRadix; k += kSortThreads)
