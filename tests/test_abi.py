@@ -86,6 +86,22 @@ def test_host_side_argument_checks(lib_path, bad):
     assert e.value.status == expect
 
 
+@pytest.mark.parametrize("batch,ok", [(0, True), (32, True), (64, True), (128, True), (192, True), (96, False),
+                                      (256, False)])
+def test_staging_batch_sizes(lib_path, batch, ok):
+    """The forward stages 32, 64, 128 or 192 records per batch (0 means the
+    default); any other count is refused on the host."""
+    from paper_2410_08129_gb300 import binding as B
+    _, cam, prm, tile = scenes.config1()
+    launch = B.c_launch(tile, smem_batch=batch)
+    if ok:
+        assert B.htgs_workspace_size(256, cam, prm, launch, 1 << 16)[0] > 0
+    else:
+        with pytest.raises(B.HTGSError) as e:
+            B.htgs_workspace_size(256, cam, prm, launch, 1 << 16)
+        assert e.value.status == B.HTGS_ERR_NOT_SUPPORTED
+
+
 def test_oracle_is_not_linked_into_the_library(lib_path):
     out = subprocess.run(["nm", "-D", lib_path], capture_output=True, text=True, check=True).stdout
     assert "og_" not in out

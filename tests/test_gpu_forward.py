@@ -128,7 +128,7 @@ def test_launch_shapes_agree(cfg1, tile, ppt):
     assert np.abs(img2 - img).max() <= 1e-6
 
 
-@pytest.mark.parametrize("batch", [32, 128])
+@pytest.mark.parametrize("batch", [32, 128, 192])
 def test_smem_batch_sizes_agree(batch):
     """The records staged per shared-memory batch change only the staging:
     the traversal order and arithmetic are the same, so the image is
